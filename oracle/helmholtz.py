@@ -1,0 +1,105 @@
+"""Oracle: the discrete heterogeneous Helmholtz operator (Section 3.1, Eq. 1-3).
+
+Test infrastructure only (see the package docstring).
+
+All operators here act on the h^2-scaled system h^2 A u = h^2 g, so the stencil
+entries are O(1):
+
+    (h^2 A u)[i,j] = 4 u[i,j] - u[i-1,j] - u[i+1,j] - u[i,j-1] - u[i,j+1]
+                     - (omega h)^2 kappa[i,j]^2 (1 - gamma[i,j] i) u[i,j]
+
+with zero values outside 0..N-1 (zero padding = Dirichlet, Section 3.4).  Eq. (3)
+omits gamma "for simplicity"; Eq. (1) carries it, so the mass term here does.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def omega_h_for_ppw(kappa_max: float = 1.0, ppw: float = 10.0) -> float:
+    """omega*h from the points-per-wavelength rule omega*kappa*h <= 2*pi/ppw
+    (Section 3.1, after Eq. 3), taken with equality at the largest kappa
+    (shortest wavelength)."""
+    return 2.0 * np.pi / (ppw * kappa_max)
+
+
+def abl_gamma(N: int, abl: int, gamma0: float = 0.0) -> np.ndarray:
+    """Attenuation field gamma(x) = gamma0 + gamma_ABL(x) on an N x N grid.
+
+    Section 3.1: the absorbing boundary layer is a function in gamma that goes
+    from 0 to 1 towards the boundaries.  Reading: with d = distance in cells into
+    the layer (0 at the first interior index `abl`, `abl` at the outermost cell),
+    gamma_ABL = max((d_x/L)^2, (d_y/L)^2).
+    """
+    i = np.arange(N)
+    d = np.maximum(np.maximum(abl - i, i - (N - 1 - abl)), 0).astype(np.float64)
+    prof = (d / abl) ** 2 if abl > 0 else np.zeros(N)
+    return gamma0 + np.maximum(prof[:, None], prof[None, :])
+
+
+def helmholtz_mass(kappa: np.ndarray, omega_h: float, gamma: np.ndarray) -> np.ndarray:
+    """Mass term of h^2 A (Eq. 1 and 3): (omega h)^2 kappa^2 (1 - gamma i)."""
+    return (omega_h ** 2) * kappa.astype(np.float64) ** 2 * (1.0 - 1j * gamma)
+
+
+def sl_mass(kappa2: np.ndarray, omega_h: float, beta: float = 0.5, alpha: float = 1.0,
+            gamma: np.ndarray | None = None) -> np.ndarray:
+    """Mass term of the h^2-scaled shifted Laplacian (Eq. 4):
+    (omega h)^2 kappa^2 (alpha - beta i), alpha = 1, beta = 0.5 (Section 3.2).
+    If `gamma` is given (ablation flag), the shift becomes (alpha - (beta+gamma) i).
+    """
+    shift = alpha - 1j * (beta + (gamma if gamma is not None else 0.0))
+    return (omega_h ** 2) * kappa2 * shift
+
+
+def apply_stencil(mass: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = (h^2 A) x for the 5-point operator of Eq. (3) with a pointwise mass.
+
+    `x` is [..., N, M] (any leading batch dims); `mass` is [N, M].  Zero padding
+    outside the grid (Section 3.4: zero-padded convolutions = Dirichlet BC).
+    """
+    x = np.asarray(x)
+    xp = np.zeros(x.shape[:-2] + (x.shape[-2] + 2, x.shape[-1] + 2), dtype=np.result_type(x, mass))
+    xp[..., 1:-1, 1:-1] = x
+    nbr = xp[..., :-2, 1:-1] + xp[..., 2:, 1:-1] + xp[..., 1:-1, :-2] + xp[..., 1:-1, 2:]
+    return (4.0 - mass) * x - nbr
+
+
+def apply_stencil_loops(mass: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Element-by-element version of `apply_stencil` for tiny grids (brute force)."""
+    N, M = x.shape
+    y = np.zeros((N, M), dtype=np.complex128)
+    for i in range(N):
+        for j in range(M):
+            s = (4.0 - mass[i, j]) * x[i, j]
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < N and 0 <= jj < M:
+                    s -= x[ii, jj]
+            y[i, j] = s
+    return y
+
+
+class Problem:
+    """One slowness model with its frequency and absorbing layer.
+
+    kappa   : float64 [N][N] slowness (including the absorbing layer cells)
+    abl     : layer width in cells
+    omega_h : omega * h (dimensionless); default from the 10 points-per-wavelength rule
+    gamma0  : constant attenuation (0 at solve time, 0.05 when generating training
+              data, Section 4.3)
+    """
+
+    def __init__(self, kappa: np.ndarray, abl: int, omega_h: float | None = None,
+                 gamma0: float = 0.0):
+        self.kappa = np.asarray(kappa, dtype=np.float64)
+        self.N = self.kappa.shape[0]
+        assert self.kappa.shape == (self.N, self.N)
+        self.abl = abl
+        self.omega_h = omega_h_for_ppw(self.kappa.max()) if omega_h is None else omega_h
+        self.gamma = abl_gamma(self.N, abl, gamma0)
+        self.mass_A = helmholtz_mass(self.kappa, self.omega_h, self.gamma)
+
+    def A(self, x: np.ndarray) -> np.ndarray:
+        """h^2 A x (Eq. 3 with gamma)."""
+        return apply_stencil(self.mass_A, x)

@@ -1,0 +1,131 @@
+"""Pins of the oracle's encoder-solver network (Sections 4.1-4.4, 5.3): gradients
+against central finite differences, shapes and parameter counts printed in the
+paper, BatchNorm folding, and the data-generation / loss / Adam steps (no GPU)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cnn
+from oracle import helmholtz as hz
+from oracle import multigrid as mg
+from oracle import training as tr
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def _setup(I=32, B=2, c0=4, seed=1):
+    P = synth.random_params(cnn.param_spec(c0), seed=seed, bn_jitter=0.2)
+    net = cnn.Network(P, c0=c0)
+    abl = 4
+    prob = hz.Problem(synth.grf_kappa(I - 2 * abl, abl, 4.0, seed + 1), abl)
+    kf = cnn.kappa_features(prob.kappa, prob.gamma)
+    r = synth.random_complex((B, I, I), seed + 2)
+    et = 0.01 * synth.random_complex((B, I, I), seed + 3)
+    return net, P, kf, r, et
+
+
+@pytest.mark.parametrize("skip", [True, False])
+def test_network_gradients_match_central_differences(skip):
+    """Every parameter tensor: directional derivative of the Eq. (16) loss along a
+    random direction, analytic vs central differences (FP64), relative 1e-6."""
+    net, P, kf, r, et = _setup()
+
+    def loss_of(params):
+        net.params = params
+        e, _ = net.forward(r, kf, train=True, skip=skip)
+        return tr.mse_loss(e, et)[0]
+
+    net.params = P
+    e, tp = net.forward(r, kf, train=True, skip=skip, record=True)
+    L, ge = tr.mse_loss(e, et)
+    grads = net.backward(tp, ge)
+    rng = np.random.default_rng(0)
+    assert set(grads) == set(P)
+    for name in P:
+        d = rng.standard_normal(P[name].shape)
+        # 4-point central difference (truncation O(h^4))
+        vals = []
+        for c in (2, 1, -1, -2):
+            Q = dict(P)
+            Q[name] = P[name] + c * 1e-4 * d
+            vals.append(loss_of(Q))
+        fd = (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * 1e-4)
+        an = float((grads[name] * d).sum())
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-10 * abs(L)), (name, fd, an)
+
+
+def test_parameter_count_and_feature_shapes_match_paper():
+    n_solver = sum(int(np.prod(s)) for n, s, *_ in cnn.param_spec(16) if n.startswith("s."))
+    ref = GOLD["solver_params"]["value"]
+    assert abs(n_solver - ref) / ref < 0.03          # 360K (Table 4)
+    P = synth.random_params(cnn.param_spec(16), seed=0)
+    net = cnn.Network(P, c0=16)
+    I = 64
+    tp = cnn.Tape(P, record=False)
+    kf = cnn.Var(np.zeros((1, 2, I, I)))
+    encs = cnn.encoder(tp, kf, False, net.running)
+    for (c, div), enc in zip(GOLD["encoder_feature_maps"]["value"], encs):
+        assert enc.a.shape == (1, c, I // div, I // div)
+    assert cnn.coarsest_size(1024) == 1024 // GOLD["solver_coarsest"]["value"][1]
+    assert cnn.coarsest_size(256) == 256 // 8
+    assert cnn.skip_last_down(GOLD["skip_threshold"]["value"] - 1)
+    assert not cnn.skip_last_down(GOLD["skip_threshold"]["value"])
+
+
+def test_bn_eval_folding_equivalence():
+    """Eval-mode BN equals the folded affine a*x + c."""
+    rng = np.random.default_rng(3)
+    P = {"bn.g": rng.uniform(0.5, 2, 5), "bn.b": rng.standard_normal(5)}
+    running = {"bn": (rng.standard_normal(5), rng.uniform(0.5, 2, 5))}
+    x = rng.standard_normal((2, 5, 3, 3))
+    tp = cnn.Tape(P, record=False)
+    y = cnn.batchnorm(tp, cnn.Var(x), "bn", False, running).a
+    a, c = cnn.fold_bn(P, running, "bn")
+    assert np.allclose(y, a[None, :, None, None] * x + c[None, :, None, None])
+
+
+def test_eval_forward_is_scale_equivariant_and_zero_safe():
+    """Reading A10: e = ||r|| Net(r/||r||), so Net(c r) = |c| ... for c > 0."""
+    net, P, kf, r, _ = _setup(B=2)
+    e1, _ = net.forward(r, kf, train=False)
+    e2, _ = net.forward(3.0 * r, kf, train=False)
+    assert np.allclose(e2, 3.0 * e1, rtol=1e-12)
+    z, _ = net.forward(np.zeros_like(r), kf, train=False)
+    assert np.all(np.isfinite(z)) and np.allclose(z, 0.0)
+
+
+def test_training_pairs_satisfy_r_equals_A_e():
+    """Eq. (17): r = b - A x_tilde = A e with e = x - x_tilde."""
+    N, abl = 32, 4
+    prob = hz.Problem(synth.grf_kappa(N - 2 * abl, abl, 4.0, 2), abl, gamma0=GOLD["train_gamma"]["value"])
+    M = mg.SLMultigrid(prob, 3)
+    x = synth.smooth_plus_noise(3, N, seed=4)
+    k = np.array([2, 5, 20])
+    e, r = tr.generate_pairs(prob, M, x, k)
+    for i in range(3):
+        assert np.allclose(r[i], prob.A(e[i]), atol=1e-12 * np.abs(r[i]).max())
+    # more V-cycle iterations leave a smaller residual relative to b = A x
+    rel = [np.linalg.norm(r[i]) / np.linalg.norm(prob.A(x[i])) for i in range(3)]
+    assert rel[2] < rel[0]
+    en, rn = tr.normalise_pairs(e, r)
+    assert np.allclose([np.linalg.norm(v) for v in rn], 1.0)
+
+
+def test_mse_loss_gradient_and_adam_first_step():
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((3, 4, 4)) + 1j * rng.standard_normal((3, 4, 4))
+    b = rng.standard_normal((3, 4, 4)) + 1j * rng.standard_normal((3, 4, 4))
+    L, g = tr.mse_loss(a, b)
+    assert np.isclose(L, (np.abs(a - b) ** 2).sum() / 3)
+    h = 1e-7
+    ap = a.copy(); ap[1, 2, 3] += h
+    assert np.isclose((tr.mse_loss(ap, b)[0] - L) / h, g[1, 2, 3].real, rtol=1e-5)
+    # Adam's first step moves each weight by -lr * sign(g) (bias-corrected moments)
+    params = {"w": np.array([1.0, -2.0, 0.5])}
+    grads = {"w": np.array([0.3, -4.0, 1e-3])}
+    tr.adam_step(params, grads, {}, lr=GOLD["adam_lr"]["value"])
+    step = params["w"] - np.array([1.0, -2.0, 0.5])
+    assert np.allclose(step, -1e-3 * np.sign(grads["w"]), rtol=1e-4)
