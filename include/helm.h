@@ -1,0 +1,190 @@
+/*
+ * helm.h - C ABI of the GB300 (sm_103a) library for the learned multigrid-augmented
+ * Helmholtz solver of Lerer, Ben-Yair and Treister (arXiv 2306.17486).
+ *
+ * The library solves the h^2-scaled discrete heterogeneous Helmholtz system
+ *
+ *     h^2 A u = h^2 g,   A = -Delta_h - omega^2 kappa^2 (1 - gamma i)        (Eq. 1-3)
+ *
+ * on an nx x ny grid (zero Dirichlet values outside, absorbing layer in gamma) with
+ * flexible GMRES (Saad 1993), preconditioned either by a shifted-Laplacian multigrid
+ * V-cycle (Section 3.2, Algorithm 1, Eq. 4, 6, 8) or by the encoder-solver U-Net with
+ * its implicit coarsest layer composed with that V-cycle (Section 4).
+ *
+ * Conventions shared by every call
+ *   - Complex vectors are interleaved (re, im) float32 ("complex64") or float64
+ *     ("complex128"), row-major [batch][ny][nx], one right-hand side per batch item.
+ *   - Every pointer argument named *_dev, and every vector argument of the hot calls,
+ *     is DEVICE memory owned by the caller; the library never frees it.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Hot calls are
+ *     asynchronous and stream-ordered; they allocate nothing: scratch comes from the
+ *     caller's workspace, whose size helm_workspace_size() returns.
+ *   - Return value: HELM_OK (0) or a negative HELM_E* code; helm_last_error_string()
+ *     describes the last failure on the calling thread.  Per-right-hand-side
+ *     non-convergence is not a call error: it is reported in helm_fgmres_stats.status.
+ *   - Device kernels never spin unboundedly: a wait that times out sets a bit in the
+ *     device error word, read (and cleared) with helm_device_errors().
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------- */
+#define HELM_OK 0
+#define HELM_EINVAL (-1)     /* bad argument (null pointer, non-positive size, ...)        */
+#define HELM_ESHAPE (-2)     /* grid not divisible as required (see each call)            */
+#define HELM_ECUDA (-3)      /* a CUDA runtime / driver call failed                       */
+#define HELM_ENOMEM (-4)     /* setup allocation failed                                   */
+#define HELM_ETIMEOUT (-5)   /* a device-side bounded wait gave up (device error word set) */
+#define HELM_EWORKSPACE (-6) /* workspace smaller than helm_workspace_size()              */
+#define HELM_ESTATE (-7)     /* call made in the wrong state (e.g. backward without a
+                                training forward)                                        */
+
+/* ---- per-RHS solver status (helm_fgmres_stats.status) ---------------------------- */
+#define HELM_STATUS_ACTIVE 0
+#define HELM_STATUS_CONVERGED 1
+#define HELM_STATUS_MAXIT 2
+#define HELM_STATUS_NONFINITE 3
+
+/* ---- device error word bits ------------------------------------------------------ */
+#define HELM_DEVERR_TMA_WAIT 1u   /* a TMA completion wait ran out                       */
+#define HELM_DEVERR_MMA_WAIT 2u   /* a tensor-core completion wait ran out               */
+
+typedef struct helm_problem helm_problem; /* one slowness model + frequency + multigrid  */
+
+/* Multigrid options (Section 3.2 / 3.4). */
+typedef struct {
+  int levels;            /* grid levels incl. the finest (>= 2); nx, ny divisible by 2^levels */
+  double beta;           /* imaginary shift of Eq. (4), alpha = 1 (paper: 0.5)              */
+  double omega_jacobi;   /* damped-Jacobi weight (0.8)                                       */
+  int coarse_iters;      /* GMRES iterations with Jacobi right-preconditioning on the
+                            coarsest grid (Section 3.4; default 10, run to the full count)  */
+  int sl_includes_gamma; /* 0: SL mass (1 - beta i); 1: (1 - (beta + gamma) i)               */
+  int boundary_fix;      /* 1: coarse grids keep the low-side Dirichlet boundary at the
+                            fine position (ghost-point correction of the first row/col)     */
+} helm_mg_opts;
+
+/* Fill `o` with the defaults above (levels = 3). */
+void helm_mg_opts_default(helm_mg_opts* o);
+
+/*
+ * Create a problem (Section 3.1): copies kappa (device, float32 [ny][nx], slowness
+ * including the absorbing-layer cells), builds on the device
+ *   gamma(x) = gamma0 + max((d_x/abl)^2, (d_y/abl)^2)   (absorbing layer, quadratic ramp)
+ *   mass_A   = (omega h)^2 kappa^2 (1 - gamma i)        (fine Helmholtz operator, Eq. 3)
+ *   mass_SL,l = (omega h 2^l)^2 kappa_l^2 (1 - beta i)  (SL operator per level, Eq. 4),
+ *              kappa_l^2 the full-weighting average of kappa^2 (Eq. 8)
+ * and the damped Jacobi inverse diagonals omega_J / (4 - mass_SL,l).
+ * omega_h is omega times the grid spacing (10 points per wavelength: 2 pi / 10).
+ * Returns HELM_ESHAPE unless nx, ny are even and divisible by 2^levels.
+ * The problem owns its device arrays until helm_problem_destroy().
+ */
+int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double omega_h, double gamma0,
+                        const helm_mg_opts* opts, void* stream, helm_problem** out);
+int helm_problem_destroy(helm_problem* p);
+
+/* Grid size of multigrid level `level` (0 = finest). */
+int helm_problem_level_shape(const helm_problem* p, int level, int* nx, int* ny);
+
+/* Copy a setup field to caller device memory `out_dev` (complex64 [ny_l][nx_l] unless
+ * noted): which = 0 mass_A (level must be 0), 1 mass_SL at `level`, 2 damped inverse
+ * Jacobi diagonal at `level`, 3 gamma (float32, level 0), 4 kappa (float32, level 0). */
+int helm_problem_get_field(const helm_problem* p, int which, int level, void* out_dev, void* stream);
+
+/*
+ * Workspace bytes needed by any hot call below for `batch` right-hand sides and
+ * FGMRES restart length `restart` (cnn may be NULL: SL-multigrid only).
+ */
+typedef struct helm_cnn helm_cnn;
+int helm_workspace_size(const helm_problem* p, const helm_cnn* cnn, int batch, int restart, size_t* bytes);
+
+/*
+ * y = h^2 A x  (Eq. 3 with the absorbing-layer gamma; 5-point stencil, zero outside).
+ * x, y: complex64 [batch][ny][nx], distinct buffers.  No workspace.
+ */
+int helm_helmholtz_apply(const helm_problem* p, const void* x, void* y, int batch, void* stream);
+
+/*
+ * r = h^2 b - h^2 A x evaluated in FP64 arithmetic (the true residual of Section 5's
+ * stopping rule): b complex64, x complex128, r complex64, rnorm2_dev (nullable) receives
+ * ||r||^2 per RHS as float64 [batch].  Workspace as returned by helm_workspace_size.
+ */
+int helm_helmholtz_residual_fp64(const helm_problem* p, const void* b, const void* x, void* r,
+                                 double* rnorm2_dev, int batch, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * z = V(r): one shifted-Laplacian V(1,1) cycle from a zero initial guess (Algorithm 1
+ * applied recursively): damped Jacobi pre-sweep, full-weighting restriction of the
+ * residual, coarse correction (coarsest level: coarse_iters GMRES iterations with a
+ * Jacobi right preconditioner), bilinear prolongation, damped Jacobi post-sweep.
+ * r, z: complex64 [batch][ny][nx].  Workspace as returned by helm_workspace_size.
+ */
+int helm_slmg_vcycle(const helm_problem* p, const void* r, void* z, int batch, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* FGMRES options. */
+typedef struct {
+  int restart;      /* FGMRES(m) restart length (paper: 10)                                */
+  double rtol;      /* stop when ||b - A x|| <= rtol ||b|| (true FP64 residual)             */
+  int maxit;        /* cap on Arnoldi steps per RHS (paper: 2000)                           */
+  int warmup_iters; /* with a CNN: first cycle of this many steps with the V-cycle only
+                       (Section 4.1: typically 3); ignored without a CNN                   */
+  int reorth;       /* 0: classical Gram-Schmidt; 1: CGS with selective re-orthogonalisation
+                       (second pass when ||w|| drops below ||w_0||/sqrt 2); 2: always CGS2   */
+} helm_fgmres_opts;
+
+/* Per-RHS result. */
+typedef struct {
+  int iters;           /* Arnoldi steps performed (= preconditioner applications)         */
+  int status;          /* HELM_STATUS_*                                                   */
+  double rel_res_est;  /* last Givens residual estimate / ||b||                           */
+  double rel_res_true; /* ||b - A x|| / ||b|| in FP64 at exit                             */
+} helm_fgmres_stats;
+
+void helm_fgmres_opts_default(helm_fgmres_opts* o);
+
+/*
+ * Right-preconditioned flexible GMRES on h^2 A x = b for `batch` right-hand sides.
+ * b: complex64 [batch][ny][nx]; x: complex128 [batch][ny][nx], in: initial guess,
+ * out: solution (accumulated in FP64; the Krylov vectors are FP32).
+ * cnn: NULL for the SL V-cycle preconditioner, else the composed preconditioner
+ *   z = e + V(r - A e), e = ||r|| Net(r / ||r||)  (Section 4.1), with the warm-up cycle.
+ * maxit_dev: nullable device int [batch] per-RHS caps (min with opts->maxit).
+ * stats_dev: device helm_fgmres_stats [batch] written at exit.
+ * The call synchronises `stream` once per restart cycle to test for completion.
+ */
+int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b, void* x, int batch,
+                      const helm_fgmres_opts* opts, const int* maxit_dev, helm_fgmres_stats* stats_dev,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Number of kernels the library has launched in this process (all devices). */
+unsigned long long helm_launch_count(void);
+
+/* Opt-in profiler: between helm_profile_begin() and helm_profile_end() every kernel
+ * launch is bracketed by CUDA events on its own stream; helm_profile_end() waits for
+ * them and aggregates per kernel name.  helm_profile_read(i, ...) returns the i-th
+ * kernel name (library-owned string), its launch count and total device time (ms).
+ * Host-side only; recording adds two events per launch. */
+int helm_profile_begin(void);
+int helm_profile_end(int* nkernels);
+int helm_profile_read(int idx, const char** name, long* launches, double* total_ms);
+
+/* Read and clear the device error word (HELM_DEVERR_* bits) of the current device. */
+int helm_device_errors(unsigned int* flags);
+
+/* Human-readable description of the last error on this thread ("" if none). */
+const char* helm_last_error_string(void);
+
+/* Library version string. */
+const char* helm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

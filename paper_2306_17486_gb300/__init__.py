@@ -1,0 +1,164 @@
+"""GB300 (sm_103a) library for learned multigrid-augmented Helmholtz preconditioning
+(arXiv 2306.17486): Python binding of the C ABI in include/helm.h.
+
+This module only marshals arguments: every step of the solver runs in the CUDA
+kernels of libhelm.so.  Torch supplies device memory and streams.  There is no CPU
+fallback; without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FgmresOpts, FgmresStats, HelmError, MgOpts, check, lib
+
+STATUS = {0: "active", 1: "converged", 2: "maxit", 3: "nonfinite"}
+
+STATS_DTYPE = np.dtype([("iters", "<i4"), ("status", "<i4"), ("rel_res_est", "<f8"), ("rel_res_true", "<f8")])
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise HelmError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+
+
+def mg_opts(levels=3, beta=0.5, omega_jacobi=0.8, coarse_iters=10, sl_includes_gamma=False, boundary_fix=True):
+    o = MgOpts()
+    lib().helm_mg_opts_default(C.byref(o))
+    o.levels, o.beta, o.omega_jacobi = levels, beta, omega_jacobi
+    o.coarse_iters, o.sl_includes_gamma, o.boundary_fix = coarse_iters, int(sl_includes_gamma), int(boundary_fix)
+    return o
+
+
+def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1):
+    o = FgmresOpts()
+    o.restart, o.rtol, o.maxit, o.warmup_iters, o.reorth = restart, rtol, maxit, warmup_iters, reorth
+    return o
+
+
+class Problem:
+    """One slowness model kappa (CUDA float32 [ny, nx], absorbing layer included)."""
+
+    def __init__(self, kappa: torch.Tensor, abl: int, omega_h: float, gamma0: float = 0.0, levels: int = 3,
+                 **mg):
+        _need(kappa, torch.float32, "kappa")
+        self.ny, self.nx = kappa.shape
+        self.abl, self.omega_h, self.gamma0, self.levels = abl, omega_h, gamma0, levels
+        self.device = kappa.device
+        self._opts = mg_opts(levels=levels, **mg)
+        h = C.c_void_p()
+        check(lib().helm_problem_create(_ptr(kappa), self.nx, self.ny, abl, omega_h, gamma0, C.byref(self._opts),
+                                        _stream(), C.byref(h)), "helm_problem_create")
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().helm_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_shape(self, level):
+        nx, ny = C.c_int(), C.c_int()
+        check(lib().helm_problem_level_shape(self.handle, level, C.byref(nx), C.byref(ny)), "level_shape")
+        return ny.value, nx.value
+
+    def field(self, which: str, level: int = 0) -> torch.Tensor:
+        code = {"mass_A": 0, "mass_SL": 1, "dinv_SL": 2, "gamma": 3, "kappa": 4}[which]
+        ny, nx = self.level_shape(level)
+        dt = torch.float32 if code >= 3 else torch.complex64
+        out = torch.empty((ny, nx), dtype=dt, device=self.device)
+        check(lib().helm_problem_get_field(self.handle, code, level, _ptr(out), _stream()), "get_field")
+        return out
+
+    def workspace(self, batch: int, restart: int = 10, cnn=None) -> torch.Tensor:
+        n = C.c_size_t()
+        check(lib().helm_workspace_size(self.handle, cnn.handle if cnn is not None else None, batch, restart,
+                                        C.byref(n)), "workspace_size")
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+
+def helmholtz_apply(p: Problem, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+    """y = h^2 A x for complex64 x [B, ny, nx]."""
+    _need(x, torch.complex64, "x")
+    y = torch.empty_like(x) if y is None else y
+    B = x.shape[0] if x.dim() == 3 else 1
+    check(lib().helm_helmholtz_apply(p.handle, _ptr(x), _ptr(y), B, _stream()), "helm_helmholtz_apply")
+    return y
+
+
+def helmholtz_residual_fp64(p: Problem, b: torch.Tensor, x: torch.Tensor):
+    """(r, ||r||^2) with r = b - h^2 A x evaluated in FP64 (x complex128)."""
+    _need(b, torch.complex64, "b")
+    _need(x, torch.complex128, "x")
+    B = b.shape[0] if b.dim() == 3 else 1
+    r = torch.empty_like(b)
+    nr = torch.empty(B, dtype=torch.float64, device=b.device)
+    ws = p.workspace(B)
+    check(lib().helm_helmholtz_residual_fp64(p.handle, _ptr(b), _ptr(x), _ptr(r), _ptr(nr), B, _ptr(ws),
+                                             ws.numel(), _stream()), "helm_helmholtz_residual_fp64")
+    return r, nr
+
+
+def slmg_vcycle(p: Problem, r: torch.Tensor, z: torch.Tensor | None = None) -> torch.Tensor:
+    """z = V(r), one shifted-Laplacian V(1,1) cycle."""
+    _need(r, torch.complex64, "r")
+    z = torch.empty_like(r) if z is None else z
+    B = r.shape[0] if r.dim() == 3 else 1
+    ws = p.workspace(B)
+    check(lib().helm_slmg_vcycle(p.handle, _ptr(r), _ptr(z), B, _ptr(ws), ws.numel(), _stream()),
+          "helm_slmg_vcycle")
+    return z
+
+
+def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn=None, restart=10, rtol=1e-6,
+                 maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None):
+    """Solve h^2 A x = b (b complex64 [B, ny, nx]); x complex128 (in: x0, out: solution).
+    Returns (x, stats) with stats a numpy structured array (iters, status, rel_res_est,
+    rel_res_true) per right-hand side."""
+    _need(b, torch.complex64, "b")
+    B = b.shape[0]
+    if x is None:
+        x = torch.zeros(b.shape, dtype=torch.complex128, device=b.device)
+    _need(x, torch.complex128, "x")
+    stats = torch.zeros(B * STATS_DTYPE.itemsize, dtype=torch.uint8, device=b.device)
+    ws = p.workspace(B, restart, cnn)
+    o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth)
+    caps = None
+    if maxit_per_rhs is not None:
+        _need(maxit_per_rhs, torch.int32, "maxit_per_rhs")
+        caps = maxit_per_rhs
+    check(lib().helm_fgmres_solve(p.handle, cnn.handle if cnn is not None else None, _ptr(b), _ptr(x), B,
+                                  C.byref(o), _ptr(caps), _ptr(stats), _ptr(ws), ws.numel(), _stream()),
+          "helm_fgmres_solve")
+    st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=STATS_DTYPE)
+    return x, st
+
+
+def device_errors() -> int:
+    f = C.c_uint()
+    check(lib().helm_device_errors(C.byref(f)), "helm_device_errors")
+    return f.value
+
+
+def version() -> str:
+    return lib().helm_version().decode()

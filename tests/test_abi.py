@@ -1,0 +1,49 @@
+"""The C-ABI library builds, loads and exports every symbol include/helm.h declares
+(no GPU: nothing here calls a compute entry point)."""
+import ctypes
+import os
+
+import pytest
+
+import __graft_entry__
+from paper_2306_17486_gb300 import _lib
+
+
+@pytest.fixture(scope="module")
+def L():
+    __graft_entry__.build()
+    return _lib.lib()
+
+
+def test_header_symbols_exported(L):
+    names = _lib.header_functions()
+    assert "helm_fgmres_solve" in names and "helm_slmg_vcycle" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # every exported declaration has a ctypes prototype in the binding
+    assert not [n for n in names if n not in _lib.PROTOS]
+
+
+def test_host_side_validation_without_gpu(L):
+    # argument checks run on the host before any CUDA call
+    assert L.helm_problem_create(None, 64, 64, 8, 0.6, 0.0, None, None, ctypes.byref(ctypes.c_void_p())) == -1
+    assert b"invalid" in L.helm_last_error_string()
+    o = _lib.MgOpts()
+    L.helm_mg_opts_default(ctypes.byref(o))
+    assert (o.levels, o.beta, o.omega_jacobi, o.coarse_iters, o.boundary_fix) == (3, 0.5, 0.8, 10, 1)
+    o.levels = 4
+    # 100 is not divisible by 2^4: shape error, before touching the device
+    fake = ctypes.c_void_p(0x1000)
+    assert L.helm_problem_create(fake, 100, 100, 8, 0.6, 0.0, ctypes.byref(o), None,
+                                 ctypes.byref(ctypes.c_void_p())) == -2
+    f = _lib.FgmresOpts()
+    L.helm_fgmres_opts_default(ctypes.byref(f))
+    assert (f.restart, f.rtol, f.maxit, f.warmup_iters) == (10, 1e-6, 2000, 3)
+    assert L.helm_version().startswith(b"helm-gb300")
+    assert ctypes.sizeof(_lib.FgmresStats) == 24
+
+
+def test_library_is_in_tree_and_built_for_sm103a(L):
+    assert os.path.dirname(_lib.LIB_PATH).startswith(os.path.dirname(os.path.abspath(_lib.__file__)))
+    from paper_2306_17486_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
