@@ -56,6 +56,12 @@ extern "C" {
 #define HELM_DEVERR_TMA_WAIT 1u   /* a TMA completion wait ran out                       */
 #define HELM_DEVERR_MMA_WAIT 2u   /* a tensor-core completion wait ran out               */
 
+/* ---- convolution modes (helm_conv_bf16) ----------------------------------------- */
+#define HELM_CONV_S1 0 /* 3x3, stride 1, zero padding 1                                  */
+#define HELM_CONV_S2 1 /* 3x3, stride 2, padding 1: output H/2 x W/2                      */
+#define HELM_CONV_T2 2 /* 3x3 transposed, stride 2, padding 1, output padding 1: 2H x 2W  */
+#define HELM_CONV_T1 3 /* 3x3 transposed, stride 1, padding 1 (= S1 with flipped kernel)  */
+
 typedef struct helm_problem helm_problem; /* one slowness model + frequency + multigrid  */
 
 /* Multigrid options (Section 3.2 / 3.4). */
@@ -163,6 +169,22 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b,
                       const helm_fgmres_opts* opts, const int* maxit_dev, helm_fgmres_stats* stats_dev,
                       void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * One convolution of the encoder-solver network on the tcgen05 tensor cores
+ * (Sections 4.4, 5.3): x BF16 NHWC [batch][hi][wi][cin], w FP32 in the layout of the
+ * paper's PyTorch modules ([cout][cin][3][3] for S1/S2, [cin][cout][3][3] for T1/T2,
+ * [cout][cin] when taps == 1), packed to BF16 in `ws`.  Output
+ *   y    = act(scale * acc + shift) + add1 + add2   (BF16 NHWC, nullable)
+ *   yraw = acc                                      (FP32 NHWC, nullable)
+ * scale/shift nullable (1, 0); act 1 = softplus; add1 [batch][ho][wo][cout] BF16,
+ * add2 the same or [1][ho][wo][cout] with add2_bcast = 1 (both nullable).
+ * cin <= 2 or a multiple of 8 (one of the network's layer shapes); cout a multiple
+ * of 16.  HELM_EINVAL for shapes without a kernel instance.
+ */
+int helm_conv_bf16(const void* x, int batch, int hi, int wi, int cin, const float* w, int cout, int taps, int mode,
+                   const float* scale, const float* shift, int act, const void* add1, const void* add2,
+                   int add2_bcast, void* y, float* yraw, void* ws, size_t ws_bytes, void* stream);
+
 /* Number of kernels the library has launched in this process (all devices). */
 unsigned long long helm_launch_count(void);
 
@@ -174,6 +196,58 @@ unsigned long long helm_launch_count(void);
 int helm_profile_begin(void);
 int helm_profile_end(int* nkernels);
 int helm_profile_read(int idx, const char** name, long* launches, double* total_ms);
+
+/* ---- the encoder-solver network (Sections 4.1-4.4, 5.3) ---------------------------- */
+typedef struct {
+  int c0;             /* channels of the first level (16; kernels exist for 16)           */
+  int expansion;      /* inverted-bottleneck expansion factor (6)                         */
+  int skip_threshold; /* grids below this size keep the coarsest level at I/8 (512)       */
+  int literal_green;  /* 0: Eq. (15) read as conj(K)/(|K|^2+eps); 1: literal K/(K^2+eps) */
+} helm_cnn_desc;
+
+/* Create a network (all parameters owned by the caller, see helm_cnn_set_params); the
+ * handle owns BN running statistics (initialised to mean 0, var 1), packed BF16
+ * weights, the Green's functions per coarsest size and the encodings of one problem. */
+int helm_cnn_create(const helm_cnn_desc* desc, helm_cnn** out);
+int helm_cnn_destroy(helm_cnn* c);
+
+/* Parameter table: a flat FP32 vector; entry idx has a name (library-owned string),
+ * ndim <= 4 dims in `shape`, and starts at element `offset`.  Conv weights use the
+ * PyTorch module layouts ([co][ci][3][3], transposed [ci][co][3][3], 1x1 [co][ci]);
+ * "s.imp.K" is [2][nk][3][3] (real, imaginary parts of the implicit kernels). */
+int helm_cnn_num_params(const helm_cnn* c, size_t* n);
+int helm_cnn_param_info(const helm_cnn* c, int idx, const char** name, int* ndim, int* shape, size_t* offset);
+/* BatchNorm table: running statistics are a flat FP32 vector, BN idx at `roff`:
+ * mean [C] then variance [C]. */
+int helm_cnn_num_bn(const helm_cnn* c, int* n);
+int helm_cnn_bn_info(const helm_cnn* c, int idx, const char** name, int* C, size_t* roff);
+
+/* Use the caller's FP32 parameter vector (device, kept alive by the caller).  Marks the
+ * derived state stale; it is rebuilt (packing, BN folding, G_hat, Eq. 15) on next use. */
+int helm_cnn_set_params(helm_cnn* c, const float* params_dev, void* stream);
+int helm_cnn_set_running(helm_cnn* c, const float* running_dev, void* stream);
+int helm_cnn_get_running(helm_cnn* c, float* out_dev, void* stream);
+
+/* Run the encoder (evaluation-mode BN) on problem p's slowness model and cache the
+ * encodings (Section 4.1: once per slowness model, reused for every RHS and
+ * iteration).  Needed again after helm_cnn_set_params. */
+int helm_cnn_set_problem(helm_cnn* c, const helm_problem* p, void* ws, size_t ws_bytes, void* stream);
+
+/* e = ||r|| Net(r / ||r||) (Eq. 16's SolverNet with the residual normalisation of
+ * this library), r, e complex64 [batch][N][N].  train = 0: evaluation-mode BN with the
+ * cached encodings.  train = 1: batch-statistics BN, encoder run on p in training mode
+ * inside the call, activations saved in `ws` for helm_cnn_precond_backward, running
+ * statistics updated (momentum 0.1). */
+int helm_cnn_apply(const helm_problem* p, helm_cnn* c, const void* r, void* e, int batch, int train, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* Copy G_hat (Eq. 15, after crop and DFT) for coarsest size m to out_dev, complex64
+ * [nk][2m][2m]; builds it if needed. */
+int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream);
+
+/* The composed preconditioner of Section 4.1: z = e + V(r - A e), e = ||r|| Net(r/||r||). */
+int helm_cnn_precond_apply(const helm_problem* p, helm_cnn* c, const void* r, void* z, int batch, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /* Read and clear the device error word (HELM_DEVERR_* bits) of the current device. */
 int helm_device_errors(unsigned int* flags);

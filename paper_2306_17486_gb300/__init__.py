@@ -162,3 +162,147 @@ def device_errors() -> int:
 
 def version() -> str:
     return lib().helm_version().decode()
+
+
+CONV_MODES = {"s1": 0, "s2": 1, "t2": 2, "t1": 3}
+
+
+def conv_bf16(x: torch.Tensor, w: torch.Tensor, mode: str = "s1", scale=None, shift=None, act=False, add1=None,
+              add2=None, raw=False):
+    """One tensor-core convolution (see helm_conv_bf16): x BF16 NHWC [B, H, W, Cin],
+    w FP32 in PyTorch module layout.  Returns (y BF16 NHWC, yraw FP32 NHWC or None)."""
+    _need(x, torch.bfloat16, "x")
+    _need(w, torch.float32, "w")
+    B, H, W, Ci = x.shape
+    taps = 1 if w.dim() == 2 else 9
+    m = CONV_MODES[mode]
+    Co = w.shape[0] if (taps == 1 or m in (0, 1)) else w.shape[1]
+    if taps == 1:
+        Ho, Wo = H, W
+    elif m == 1:
+        Ho, Wo = H // 2, W // 2
+    elif m == 2:
+        Ho, Wo = 2 * H, 2 * W
+    else:
+        Ho, Wo = H, W
+    y = torch.empty((B, Ho, Wo, Co), dtype=torch.bfloat16, device=x.device)
+    yr = torch.empty((B, Ho, Wo, Co), dtype=torch.float32, device=x.device) if raw else None
+    ws = torch.empty(taps * max(16, (Ci + 15) // 16 * 16) * Co * 2 + 4096, dtype=torch.uint8, device=x.device)
+    bc = int(add2 is not None and add2.shape[0] == 1 and B > 1)
+    check(lib().helm_conv_bf16(_ptr(x), B, H, W, Ci, _ptr(w), Co, taps, m, _ptr(scale), _ptr(shift), int(act),
+                               _ptr(add1), _ptr(add2), bc, _ptr(y), _ptr(yr), _ptr(ws), ws.numel(), _stream()),
+          "helm_conv_bf16")
+    return y, yr
+
+
+class Cnn:
+    """The encoder-solver network: FP32 parameters (`params`, a flat CUDA tensor in the
+    library's parameter order) and BN running statistics live on the device."""
+
+    def __init__(self, c0=16, expansion=6, skip_threshold=512, literal_green=False, device="cuda"):
+        d = _lib.CnnDesc()
+        d.c0, d.expansion, d.skip_threshold, d.literal_green = c0, expansion, skip_threshold, int(literal_green)
+        h = C.c_void_p()
+        check(lib().helm_cnn_create(C.byref(d), C.byref(h)), "helm_cnn_create")
+        self.handle = h
+        self.device = torch.device(device)
+        n = C.c_size_t()
+        check(lib().helm_cnn_num_params(h, C.byref(n)), "num_params")
+        self.nparams = n.value
+        self.spec = []          # (name, shape, offset)
+        i = 0
+        while True:
+            nm, nd, off = C.c_char_p(), C.c_int(), C.c_size_t()
+            shp = (C.c_int * 4)()
+            if lib().helm_cnn_param_info(h, i, C.byref(nm), C.byref(nd), shp, C.byref(off)) != 0:
+                break
+            self.spec.append((nm.value.decode(), tuple(shp[:nd.value]), off.value))
+            i += 1
+        nb = C.c_int()
+        check(lib().helm_cnn_num_bn(h, C.byref(nb)), "num_bn")
+        self.bn = []            # (name, C, roff)
+        for j in range(nb.value):
+            nm, cc, ro = C.c_char_p(), C.c_int(), C.c_size_t()
+            check(lib().helm_cnn_bn_info(h, j, C.byref(nm), C.byref(cc), C.byref(ro)), "bn_info")
+            self.bn.append((nm.value.decode(), cc.value, ro.value))
+        self.nrunning = sum(2 * c for _, c, _ in self.bn)
+        self.params = torch.zeros(self.nparams, dtype=torch.float32, device=self.device)
+        self.running = torch.zeros(self.nrunning, dtype=torch.float32, device=self.device)
+        check(lib().helm_cnn_get_running(h, _ptr(self.running), _stream()), "get_running")
+        self.set_params()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().helm_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- parameters -------------------------------------------------------------
+    def set_params(self, flat: torch.Tensor | None = None):
+        if flat is not None:
+            self.params.copy_(flat)
+        check(lib().helm_cnn_set_params(self.handle, _ptr(self.params), _stream()), "set_params")
+
+    def load_dict(self, pdict: dict):
+        """Fill the parameter vector from a name -> array dict (shapes must match)."""
+        flat = np.zeros(self.nparams, dtype=np.float32)
+        for name, shape, off in self.spec:
+            a = np.asarray(pdict[name], dtype=np.float32)
+            assert a.shape == shape, (name, a.shape, shape)
+            flat[off:off + a.size] = a.ravel()
+        self.params.copy_(torch.from_numpy(flat))
+        self.set_params()
+
+    def to_dict(self, flat: torch.Tensor | None = None) -> dict:
+        v = (self.params if flat is None else flat).detach().cpu().numpy().astype(np.float64)
+        return {name: v[off:off + int(np.prod(shape))].reshape(shape) for name, shape, off in self.spec}
+
+    def load_running(self, rdict: dict):
+        """rdict: bn name -> (mean, var)."""
+        flat = np.zeros(self.nrunning, dtype=np.float32)
+        for name, c, ro in self.bn:
+            mu, var = rdict[name]
+            flat[ro:ro + c] = mu
+            flat[ro + c:ro + 2 * c] = var
+        self.running.copy_(torch.from_numpy(flat))
+        check(lib().helm_cnn_set_running(self.handle, _ptr(self.running), _stream()), "set_running")
+
+    def running_dict(self) -> dict:
+        check(lib().helm_cnn_get_running(self.handle, _ptr(self.running), _stream()), "get_running")
+        v = self.running.cpu().numpy().astype(np.float64)
+        return {name: (v[ro:ro + c].copy(), v[ro + c:ro + 2 * c].copy()) for name, c, ro in self.bn}
+
+    def ghat(self, m: int) -> torch.Tensor:
+        nk = dict((n, s) for n, s, _ in self.spec)["s.imp.K"][1]
+        out = torch.empty((nk, 2 * m, 2 * m), dtype=torch.complex64, device=self.device)
+        check(lib().helm_cnn_get_ghat(self.handle, m, _ptr(out), _stream()), "get_ghat")
+        return out
+
+    # ---- application ------------------------------------------------------------
+    def set_problem(self, p: Problem):
+        check(lib().helm_cnn_set_problem(self.handle, p.handle, None, 0, _stream()), "helm_cnn_set_problem")
+
+    def apply(self, p: Problem, r: torch.Tensor, train: bool = False, ws: torch.Tensor | None = None):
+        """e = ||r|| Net(r / ||r||)."""
+        _need(r, torch.complex64, "r")
+        B = r.shape[0]
+        e = torch.empty_like(r)
+        ws = p.workspace(B, 10, self) if ws is None else ws
+        check(lib().helm_cnn_apply(p.handle, self.handle, _ptr(r), _ptr(e), B, int(train), _ptr(ws), ws.numel(),
+                                   _stream()), "helm_cnn_apply")
+        return e
+
+    def precond(self, p: Problem, r: torch.Tensor):
+        """z = e + V(r - A e)."""
+        _need(r, torch.complex64, "r")
+        B = r.shape[0]
+        z = torch.empty_like(r)
+        ws = p.workspace(B, 10, self)
+        check(lib().helm_cnn_precond_apply(p.handle, self.handle, _ptr(r), _ptr(z), B, _ptr(ws), ws.numel(),
+                                           _stream()), "helm_cnn_precond_apply")
+        return z

@@ -56,6 +56,8 @@ PROTOS = {
     "helm_profile_begin": (i32, []),
     "helm_profile_end": (i32, [C.POINTER(i32)]),
     "helm_profile_read": (i32, [i32, C.POINTER(C.c_char_p), C.POINTER(C.c_long), C.POINTER(f64)]),
+    "helm_conv_bf16": (i32, [vp, i32, i32, i32, i32, vp, i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp, vp, sz,
+                              vp]),
     "helm_cnn_create": (i32, [C.POINTER(CnnDesc), C.POINTER(vp)]),
     "helm_cnn_destroy": (i32, [vp]),
     "helm_cnn_num_params": (i32, [vp, C.POINTER(sz)]),
@@ -66,6 +68,7 @@ PROTOS = {
     "helm_cnn_set_running": (i32, [vp, vp, vp]),
     "helm_cnn_get_running": (i32, [vp, vp, vp]),
     "helm_cnn_set_problem": (i32, [vp, vp, vp, sz, vp]),
+    "helm_cnn_get_ghat": (i32, [vp, i32, vp, vp]),
     "helm_cnn_apply": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp]),
     "helm_cnn_precond_apply": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
     "helm_cnn_precond_backward": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),

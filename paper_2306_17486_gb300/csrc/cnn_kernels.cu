@@ -1,0 +1,452 @@
+// CUDA-core kernels of the encoder-solver network (forward): encoder input
+// features, residual normalisation and fixed restriction, depthwise 3x3, the
+// implicit layer (Eq. 14) in shared memory, the Green's function of a learned kernel
+// (Eq. 15), and the projection + bilinear upsampling that ends the solver.
+#include <cuda_bf16.h>
+
+#include "cnn_kern.h"
+
+namespace helm {
+
+using bf16 = __nv_bfloat16;
+
+// ---- encoder input: (Re, Im) of kappa^2 (1 - gamma i) ------------------------------
+__global__ void k_kfeat(const float* __restrict__ kappa, const float* __restrict__ gamma, long n,
+                        bf16* __restrict__ out) {
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const float k2 = kappa[i] * kappa[i];
+    out[2 * i] = __float2bfloat16_rn(k2);
+    out[2 * i + 1] = __float2bfloat16_rn(-k2 * gamma[i]);
+  }
+}
+
+// ---- ||r_b||^2 partial sums and the final scale s_b = ||r_b|| ----------------------
+__global__ void k_norm_partial(const float2* __restrict__ r, long n, int nblk, double* __restrict__ part) {
+  const int b = blockIdx.y;
+  const long chunk = (n + nblk - 1) / nblk;
+  const long p0 = blockIdx.x * chunk, p1 = min(p0 + chunk, n);
+  double acc = 0.0;
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    float2 v = r[b * n + p];
+    acc += static_cast<double>(v.x) * v.x + static_cast<double>(v.y) * v.y;
+  }
+  acc = warp_sum(acc);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (blockDim.x >> 5); ++w) t += red[w];
+    part[static_cast<long>(b) * nblk + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_norm_final(const double* __restrict__ part, int nblk, int B, float* __restrict__ s,
+                             float* __restrict__ inv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double t = 0;
+  for (int i = 0; i < nblk; ++i) t += part[static_cast<long>(b) * nblk + i];
+  const double v = sqrt(t);
+  s[b] = static_cast<float>(v);
+  inv[b] = v > 0.0 ? static_cast<float>(1.0 / v) : 0.f;
+}
+
+// x0[b][J][K][0..1] = (Re, Im) of I_h^H (r_b / s_b): full weighting, zero padding
+__global__ void k_prep_restrict(const float2* __restrict__ r, int N, int B, const float* __restrict__ inv,
+                                bf16* __restrict__ x0) {
+  const int Nc = N / 2;
+  const long total = static_cast<long>(B) * Nc * Nc;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(i / (static_cast<long>(Nc) * Nc));
+    const int J = static_cast<int>((i / Nc) % Nc), K = static_cast<int>(i % Nc);
+    const float2* rb = r + static_cast<long>(b) * N * N;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int c = -1; c <= 1; ++c) {
+        const int y = 2 * J + a, x = 2 * K + c;
+        if (y < 0 || y >= N || x < 0 || x >= N) continue;
+        const float w = (a == 0 ? 2.f : 1.f) * (c == 0 ? 2.f : 1.f) * (1.f / 16.f);
+        const float2 v = rb[static_cast<long>(y) * N + x];
+        acc.x += w * v.x;
+        acc.y += w * v.y;
+      }
+    const float sc = inv[b];
+    x0[2 * i] = __float2bfloat16_rn(acc.x * sc);
+    x0[2 * i + 1] = __float2bfloat16_rn(acc.y * sc);
+  }
+}
+
+// ---- depthwise 3x3 (stride 1, zero padding): thread per (pixel, 8-channel group) ----
+// y = act(scale * acc + shift) (bf16) and/or the raw accumulator (fp32)
+__global__ void k_dw3x3(const bf16* __restrict__ x, int B, int H, int W, int C, const float* __restrict__ w,
+                        const float* __restrict__ scale, const float* __restrict__ shift, int act,
+                        bf16* __restrict__ y, float* __restrict__ yraw) {
+  const int G = C / 8;
+  const long total = static_cast<long>(B) * H * W * G;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int g = static_cast<int>(i % G);
+    const long pix = i / G;
+    const int xx = static_cast<int>(pix % W), yy = static_cast<int>((pix / W) % H);
+    const int b = static_cast<int>(pix / (static_cast<long>(W) * H));
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty) {
+      const int sy = yy + ty - 1;
+      if (sy < 0 || sy >= H) continue;
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) {
+        const int sx = xx + tx - 1;
+        if (sx < 0 || sx >= W) continue;
+        uint4 u = *reinterpret_cast<const uint4*>(x + ((static_cast<long>(b) * H + sy) * W + sx) * C + 8 * g);
+        const bf16* e8 = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = fmaf(w[(8 * g + e) * 9 + ty * 3 + tx], __bfloat162float(e8[e]), acc[e]);
+      }
+    }
+    if (yraw) {
+      float4* o = reinterpret_cast<float4*>(yraw + pix * C + 8 * g);
+      o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+    if (y) {
+      uint4 o;
+      bf16* ob = reinterpret_cast<bf16*>(&o);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = 8 * g + e;
+        float t = fmaf(acc[e], scale ? scale[c] : 1.f, shift ? shift[c] : 0.f);
+        if (act) t = fmaxf(t, 0.f) + log1pf(__expf(-fabsf(t)));
+        ob[e] = __float2bfloat16_rn(t);
+      }
+      *reinterpret_cast<uint4*>(y + pix * C + 8 * g) = o;
+    }
+  }
+}
+
+// ---- implicit layer (Eq. 14), one CTA per (sample, complex channel) -----------------
+// x: channels k (Re) and k + C/2 (Im) of an m x m map; zero-pad to 2m x 2m, DFT,
+// multiply by G_hat_k, inverse DFT, keep the top-left m x m block.  The DFTs are
+// evaluated as dense sums with a twiddle table, skipping the zero half of the
+// padded input and the discarded half of the output.
+// Optionally (gh_out != null) also writes conj(X_hat) . F(pad(gy)) / (2m)^2 for the
+// kernel gradient (backward; then x is the forward input and gy the output gradient).
+template <typename TIn>
+__device__ __forceinline__ float2 load_pair(const TIn* p, long idx, int C, int k) {
+  return make_float2(static_cast<float>(p[idx * C + k]), static_cast<float>(p[idx * C + k + C / 2]));
+}
+template <>
+__device__ __forceinline__ float2 load_pair<bf16>(const bf16* p, long idx, int C, int k) {
+  return make_float2(__bfloat162float(p[idx * C + k]), __bfloat162float(p[idx * C + k + C / 2]));
+}
+
+// forward DFT of the zero-padded m x m block in `X` (m x m) into `F` (2m x 2m), using
+// scratch `R` (m x 2m); twiddle W[e] = exp(-2 pi i e / 2m)
+__device__ void dft_pad_forward(const float2* X, float2* R, float2* F, const float2* Wt, int m) {
+  const int n = 2 * m;
+  for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
+    const int r = i / n, u = i % n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < m; ++c) acc = cadd(acc, cmul(X[r * m + c], Wt[(u * c) % n]));
+    R[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int v = i / n, u = i % n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < m; ++r) acc = cadd(acc, cmul(R[r * n + u], Wt[(v * r) % n]));
+    F[i] = acc;
+  }
+  __syncthreads();
+}
+
+// inverse DFT of F (2m x 2m) keeping the top-left m x m block, scaled by 1/(2m)^2
+__device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const float2* Wt, int m) {
+  const int n = 2 * m;
+  for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
+    const int r = i / n, u = i % n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int v = 0; v < n; ++v) {
+      const float2 t = Wt[(v * r) % n];
+      acc = cadd(acc, cmul(F[v * n + u], make_float2(t.x, -t.y)));
+    }
+    R[i] = acc;
+  }
+  __syncthreads();
+  const float sc = 1.f / static_cast<float>(n * n);
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    const int r = i / m, c = i % m;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int u = 0; u < n; ++u) {
+      const float2 t = Wt[(u * c) % n];
+      acc = cadd(acc, cmul(R[r * n + u], make_float2(t.x, -t.y)));
+    }
+    Y[i] = cscale(acc, sc);
+  }
+  __syncthreads();
+}
+
+template <typename TIn, typename TOut>
+__global__ void k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat, int conj_g,
+                           TOut* __restrict__ y, int accumulate) {
+  const int b = blockIdx.y, k = blockIdx.x;
+  const int n = 2 * m;
+  extern __shared__ float2 ism[];
+  float2* Wt = ism;               // n
+  float2* X = Wt + n;             // m*m   (input, later output)
+  float2* R = X + m * m;          // m*n   scratch
+  float2* F = R + m * n;          // n*n
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    float s, c;
+    sincospif(-2.f * e / n, &s, &c);
+    Wt[e] = make_float2(c, s);
+  }
+  const long base = static_cast<long>(b) * m * m;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) X[i] = load_pair<TIn>(x, base + i, C, k);
+  __syncthreads();
+  dft_pad_forward(X, R, F, Wt, m);
+  const float2* G = ghat + static_cast<long>(k) * n * n;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    float2 g = G[i];
+    if (conj_g) g.y = -g.y;
+    F[i] = cmul(F[i], g);
+  }
+  __syncthreads();
+  dft_crop_inverse(F, R, X, Wt, m);
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    const long idx = (base + i) * C;
+    if constexpr (sizeof(TOut) == 2) {
+      y[idx + k] = __float2bfloat16_rn(X[i].x);
+      y[idx + k + C / 2] = __float2bfloat16_rn(X[i].y);
+    } else {
+      if (accumulate) {
+        y[idx + k] += X[i].x;
+        y[idx + k + C / 2] += X[i].y;
+      } else {
+        y[idx + k] = X[i].x;
+        y[idx + k + C / 2] = X[i].y;
+      }
+    }
+  }
+}
+
+// ---- Green's function of a learned 3x3 kernel (Eq. 15), one CTA per channel ---------
+// Kpar: [2][nk][3][3] (real, imaginary parts).  n6 = 6m periodic grid, source at the
+// centre: G at offsets d (|d| <= m) is (1/n6^2) sum_{u,v} H(u,v) e^{+2 pi i (u dy + v dx)/n6}
+// with H = conj(Kh)/(|Kh|^2 + eps) (or Kh/(Kh^2 + eps)); crop to offsets -m..m-1 with
+// offset 0 at index 0, then G_hat = DFT_{2m}.  scratch: n6*n6 (H) + n6*2m (T) complex.
+__global__ void k_greens(const float* __restrict__ Kpar, int nk, int m, float eps, int literal,
+                         float2* __restrict__ scratch, float2* __restrict__ ghat) {
+  const int k = blockIdx.x;
+  const int n6 = 6 * m, n = 2 * m;
+  float2* H = scratch + static_cast<long>(k) * (n6 * n6 + n6 * n + n * n);
+  float2* T = H + n6 * n6;
+  float2* Gc = T + n6 * n;
+  float Kr[9], Ki[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    Kr[t] = Kpar[k * 9 + t];
+    Ki[t] = Kpar[(nk + k) * 9 + t];
+  }
+  for (int i = threadIdx.x; i < n6 * n6; i += blockDim.x) {
+    const int u = i / n6, v = i % n6;
+    float2 kh = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int c = -1; c <= 1; ++c) {
+        float s, co;
+        // exp(-2 pi i (u a + v c) / n6), argument reduced mod n6 exactly in integers
+        const int e = ((u * a + v * c) % n6 + n6) % n6;
+        sincospif(-2.f * e / n6, &s, &co);
+        const int t = (a + 1) * 3 + (c + 1);
+        kh = cadd(kh, cmul(make_float2(Kr[t], Ki[t]), make_float2(co, s)));
+      }
+    float2 h;
+    if (literal) {
+      const float2 k2 = cmul(kh, kh);
+      const float2 den = make_float2(k2.x + eps, k2.y);
+      const float d2 = den.x * den.x + den.y * den.y;
+      h = make_float2((kh.x * den.x + kh.y * den.y) / d2, (kh.y * den.x - kh.x * den.y) / d2);
+    } else {
+      const float d = kh.x * kh.x + kh.y * kh.y + eps;
+      h = make_float2(kh.x / d, -kh.y / d);
+    }
+    H[i] = h;
+  }
+  __syncthreads();
+  // T[u][j] = sum_v H[u][v] e^{+2 pi i v d_j / n6}, d_j = j for j < m else j - 2m
+  for (int i = threadIdx.x; i < n6 * n; i += blockDim.x) {
+    const int u = i / n, j = i % n;
+    const int d = j < m ? j : j - n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int v = 0; v < n6; ++v) {
+      float s, co;
+      const int e = ((v * d) % n6 + n6) % n6;
+      sincospif(2.f * e / n6, &s, &co);
+      acc = cadd(acc, cmul(H[u * n6 + v], make_float2(co, s)));
+    }
+    T[i] = acc;
+  }
+  __syncthreads();
+  const float sc = 1.f / (static_cast<float>(n6) * n6);
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int ii = i / n, j = i % n;
+    const int d = ii < m ? ii : ii - n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int u = 0; u < n6; ++u) {
+      float s, co;
+      const int e = ((u * d) % n6 + n6) % n6;
+      sincospif(2.f * e / n6, &s, &co);
+      acc = cadd(acc, cmul(T[u * n + j], make_float2(co, s)));
+    }
+    Gc[i] = cscale(acc, sc);
+  }
+  __syncthreads();
+  // G_hat = DFT_{2m}(Gc): rows then columns, reusing T as scratch
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int r = i / n, q = i % n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j < n; ++j) {
+      float s, co;
+      sincospif(-2.f * ((q * j) % n) / n, &s, &co);
+      acc = cadd(acc, cmul(Gc[r * n + j], make_float2(co, s)));
+    }
+    T[i] = acc;
+  }
+  __syncthreads();
+  float2* out = ghat + static_cast<long>(k) * n * n;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int p = i / n, q = i % n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < n; ++r) {
+      float s, co;
+      sincospif(-2.f * ((p * r) % n) / n, &s, &co);
+      acc = cadd(acc, cmul(T[r * n + q], make_float2(co, s)));
+    }
+    out[i] = acc;
+  }
+}
+
+// ---- projection 1x1 (C -> 2, + bias) at I/2, bilinear prolongation to I, times s ----
+__global__ void k_proj_prolong(const bf16* __restrict__ u, int B, int Nc, int C, const float* __restrict__ w,
+                               const float* __restrict__ bias, const float* __restrict__ s,
+                               float2* __restrict__ e) {
+  const int N = 2 * Nc;
+  const long total = static_cast<long>(B) * N * N;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(i / (static_cast<long>(N) * N));
+    const int Y = static_cast<int>((i / N) % N), X = static_cast<int>(i % N);
+    float2 acc = make_float2(0.f, 0.f);
+    const int jy0 = Y >> 1, jx0 = X >> 1;
+    const int ny = (Y & 1) ? 2 : 1, nx = (X & 1) ? 2 : 1;
+    const float wy = (Y & 1) ? 0.5f : 1.f, wx = (X & 1) ? 0.5f : 1.f;
+    for (int a = 0; a < ny; ++a) {
+      const int J = jy0 + a;
+      if (J >= Nc) continue;
+      for (int c = 0; c < nx; ++c) {
+        const int K = jx0 + c;
+        if (K >= Nc) continue;
+        const bf16* up = u + ((static_cast<long>(b) * Nc + J) * Nc + K) * C;
+        float p0 = bias[0], p1 = bias[1];
+        for (int ch = 0; ch < C; ++ch) {
+          const float v = __bfloat162float(up[ch]);
+          p0 = fmaf(w[ch], v, p0);
+          p1 = fmaf(w[C + ch], v, p1);
+        }
+        acc.x += wy * wx * p0;
+        acc.y += wy * wx * p1;
+      }
+    }
+    e[i] = cscale(acc, s[b]);
+  }
+}
+
+// ---- launch helpers -----------------------------------------------------------------
+static int grid_for(long n, int threads = 256) { return static_cast<int>(std::min<long>(div_up(n, threads), 8192)); }
+
+int launch_kfeat(const float* kappa, const float* gamma, long n, bf16* out, cudaStream_t st) {
+  HELM_LAUNCH("k_kfeat", st, k_kfeat<<<grid_for(n), 256, 0, st>>>(kappa, gamma, n, out));
+  HELM_CHECK_LAUNCH("k_kfeat");
+  return HELM_OK;
+}
+
+int launch_prep(const float2* r, int N, int B, double* part, float* s, float* inv, bf16* x0, cudaStream_t st) {
+  const long n = static_cast<long>(N) * N;
+  const int nblk = std::max(1, std::min(256, div_up(n, 4096)));
+  HELM_LAUNCH("k_norm_partial", st, k_norm_partial<<<dim3(nblk, B), 256, 0, st>>>(r, n, nblk, part));
+  HELM_LAUNCH("k_norm_final", st, k_norm_final<<<div_up(B, 64), 64, 0, st>>>(part, nblk, B, s, inv));
+  HELM_LAUNCH("k_prep_restrict", st,
+              k_prep_restrict<<<grid_for(static_cast<long>(B) * (N / 2) * (N / 2)), 256, 0, st>>>(r, N, B, inv, x0));
+  HELM_CHECK_LAUNCH("prep");
+  return HELM_OK;
+}
+
+int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const float* scale, const float* shift,
+              int act, bf16* y, float* yraw, cudaStream_t st) {
+  HELM_LAUNCH("k_dw3x3", st,
+              k_dw3x3<<<grid_for(static_cast<long>(B) * H * W * (C / 8)), 256, 0, st>>>(x, B, H, W, C, w, scale,
+                                                                                         shift, act, y, yraw));
+  HELM_CHECK_LAUNCH("k_dw3x3");
+  return HELM_OK;
+}
+
+size_t implicit_smem(int m) { return static_cast<size_t>(2 * m + m * m + m * 2 * m + 4 * m * m) * sizeof(float2); }
+
+int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat, bf16* y, cudaStream_t st) {
+  const size_t sm = implicit_smem(m);
+  if (sm > 200 * 1024) {
+    set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
+    return HELM_ESHAPE;
+  }
+  static bool attr = false;
+  if (!attr) {
+    HELM_CUDA(cudaFuncSetAttribute(k_implicit<bf16, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  HELM_LAUNCH("k_implicit", st, k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, sm, st>>>(x, m, C, ghat, 0, y, 0));
+  HELM_CHECK_LAUNCH("k_implicit");
+  return HELM_OK;
+}
+
+int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* ghat, float* gx, cudaStream_t st) {
+  const size_t sm = implicit_smem(m);
+  static bool attr = false;
+  if (!attr) {
+    HELM_CUDA(cudaFuncSetAttribute(k_implicit<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  HELM_LAUNCH("k_implicit_adj", st, k_implicit<float, float><<<dim3(C / 2, B), 256, sm, st>>>(gy, m, C, ghat, 1, gx, 1));
+  HELM_CHECK_LAUNCH("k_implicit_adj");
+  return HELM_OK;
+}
+
+size_t greens_scratch_elems(int m, int nk) {
+  const long n6 = 6 * m, n = 2 * m;
+  return static_cast<size_t>(nk) * (n6 * n6 + n6 * n + n * n);
+}
+
+int launch_greens(const float* Kpar, int nk, int m, float eps, int literal, float2* scratch, float2* ghat,
+                  cudaStream_t st) {
+  HELM_LAUNCH("k_greens", st, k_greens<<<nk, 256, 0, st>>>(Kpar, nk, m, eps, literal, scratch, ghat));
+  HELM_CHECK_LAUNCH("k_greens");
+  return HELM_OK;
+}
+
+int launch_proj(const bf16* u, int B, int Nc, int C, const float* w, const float* bias, const float* s, float2* e,
+                cudaStream_t st) {
+  const long total = static_cast<long>(B) * 4 * Nc * Nc;
+  HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<grid_for(total), 256, 0, st>>>(u, B, Nc, C, w, bias, s, e));
+  HELM_CHECK_LAUNCH("k_proj_prolong");
+  return HELM_OK;
+}
+
+}  // namespace helm

@@ -1,0 +1,426 @@
+// 3x3 and 1x1 convolutions of the encoder-solver network (Sections 4.1, 4.4, 5.3) as
+// implicit GEMMs on the tcgen05 tensor cores: BF16 NHWC activations and weights,
+// FP32 accumulation in TMEM, fused epilogue
+//     y = act(scale[c] * acc + shift[c]) + add1 + add2      (folded BN, softplus, skips)
+// or the raw FP32 accumulator (training forward, BN statistics taken afterwards).
+//
+// GEMM mapping: M = 128 output pixels per tile, N = output channels, K = taps x
+// input channels.  The output grid is flattened with a virtual pitch Po = Wo + 1 (one
+// gap column, never written), so for every 3x3 tap the 128 input rows of the A
+// operand are one contiguous window of virtual pixels shifted by dy*Po + dx; in the
+// K-major no-swizzle shared-memory layout (core matrices of 8 rows x 16 bytes) a
+// shift of the window is just a 16-byte step of the descriptor start address.  The
+// loader stages, per 8-channel group, a plane of window rows (16 B each):
+//   stride 1      : the input itself (output grid = input grid)
+//   stride 2      : four phase planes S_{py,px}(y,x) = in(2y+py, 2x+px); tap dy uses
+//                   phase (1, 0, 1)[dy+1] and shift (-1, 0, 0)[dy+1]
+//   transposed s2 : the zero-inserted upsampling up(2y, 2x) = in(y, x) at output
+//                   resolution, with the kernel flipped (dy -> 1 - ky)
+//   1x1           : 128 consecutive pixels, Po = Wo
+// One thread issues all MMAs of a tile and commits them to an mbarrier; 4 warps read
+// the accumulator with tcgen05.ld (thread t = pixel q0 + t) and run the epilogue.
+// CTAs are persistent over tiles; weights stay resident in shared memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "cnn.h"
+#include "tc.cuh"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+struct ConvArgs {
+  const bf16* x;
+  int B, Hi, Wi, Cg;     // input: batch, size, channels stored in global memory
+  int Ho, Wo, Po;        // output size, virtual pitch
+  int mode;
+  const bf16* wpk;       // packed weights [taps][G][COUT][8]
+  const float* scale;    // [COUT] or null (1)
+  const float* shift;    // [COUT] or null (0)
+  int act;               // softplus
+  const bf16* add1;      // [B][Ho][Wo][COUT] or null
+  const bf16* add2;      // [B or 1][Ho][Wo][COUT] or null
+  int add2_bcast;
+  bf16* y;               // bf16 NHWC output or null
+  float* yraw;           // fp32 NHWC raw accumulator or null
+  int tiles_per_img, ntiles;
+  int L;                 // window rows per plane
+};
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <int CS, int COUT, int TAPS>
+struct ConvCfg {
+  static constexpr int G = CS / 8;                         // 16-byte groups per pixel
+  static constexpr int NSPLIT = COUT > 256 ? 2 : 1;
+  static constexpr int NH = COUT / NSPLIT;                  // N of one MMA
+  static constexpr int NCOLS = COUT <= 32 ? 32 : COUT <= 64 ? 64 : COUT <= 128 ? 128 : COUT <= 256 ? 256 : 512;
+  static constexpr int BBYTES = TAPS * G * COUT * 16;
+  static_assert(CS % 16 == 0, "K per tap must be a multiple of 16");
+  static_assert(NH % 16 == 0 && NH <= 256, "N per MMA");
+};
+
+template <int CS, int COUT, int TAPS>
+__global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
+  using Cfg = ConvCfg<CS, COUT, TAPS>;
+  constexpr int G = Cfg::G;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + Cfg::BBYTES;
+  const int nph = (a.mode == HELM_CONV_S2) ? 4 : 1;
+  const int L = a.L;
+  float* sScale = reinterpret_cast<float*>(sA + static_cast<size_t>(nph) * G * L * 16);
+  float* sShift = sScale + COUT;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  if (warp == 0) tc::tmem_alloc(tslot, Cfg::NCOLS);
+  // weights and per-channel affine stay resident for all tiles of this CTA
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.wpk);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    for (int i = tid; i < Cfg::BBYTES / 16; i += 128) dst[i] = src[i];
+    for (int c = tid; c < COUT; c += 128) {
+      sScale[c] = a.scale ? a.scale[c] : 1.f;
+      sShift[c] = a.shift ? a.shift[c] : 0.f;
+    }
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+  constexpr uint32_t idesc = tc::idesc_bf16(128, Cfg::NH);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    const int b = tile / a.tiles_per_img;
+    const int q0 = (tile % a.tiles_per_img) * 128;
+    const bf16* xb = a.x + static_cast<long>(b) * a.Hi * a.Wi * a.Cg;
+    // ---- stage the A window (t fastest: conflict-free 16-byte shared stores) ----
+    const int total = nph * G * L;
+    for (int idx = tid; idx < total; idx += 128) {
+      const int t = idx % L;
+      const int pg = idx / L;        // phase * G + g
+      const int g = pg % G, ph = pg / G;
+      int iy = -1, ix = -1;
+      if (TAPS == 1) {
+        const int q = q0 + t;
+        const int y = q / a.Po, x = q % a.Po;
+        if (y < a.Ho) { iy = y; ix = x; }
+      } else {
+        const int q = q0 - a.Po - 1 + t;
+        const int y = floordiv(q, a.Po), x = q - y * a.Po;
+        if (y >= 0 && y < a.Ho && x < a.Wo) {
+          if (a.mode == HELM_CONV_S1) {
+            iy = y; ix = x;
+          } else if (a.mode == HELM_CONV_S2) {
+            iy = 2 * y + (ph >> 1); ix = 2 * x + (ph & 1);
+          } else {  // transposed stride 2: zero-inserted upsampling
+            if (!(y & 1) && !(x & 1)) { iy = y >> 1; ix = x >> 1; }
+          }
+        }
+      }
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (iy >= 0) {
+        const bf16* px = xb + (static_cast<long>(iy) * a.Wi + ix) * a.Cg;
+        const int c0 = 8 * g;
+        if (c0 + 8 <= a.Cg) {
+          v = *reinterpret_cast<const uint4*>(px + c0);
+        } else if (c0 < a.Cg) {
+          uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          for (int e = 0; c0 + e < a.Cg && e < 8; ++e) tmp[e] = reinterpret_cast<const uint16_t*>(px)[c0 + e];
+          v = make_uint4(tmp[0] | (tmp[1] << 16), tmp[2] | (tmp[3] << 16), tmp[4] | (tmp[5] << 16),
+                         tmp[6] | (tmp[7] << 16));
+        }
+      }
+      *reinterpret_cast<uint4*>(sA + (static_cast<size_t>(pg) * L + t) * 16) = v;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- one thread issues the MMAs of the tile ----
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t lboA = static_cast<uint32_t>(L) * 16u;
+      int kstep = 0;
+#pragma unroll 1
+      for (int tap = 0; tap < TAPS; ++tap) {
+        int row = 0, ph = 0;
+        if (TAPS == 9) {
+          const int ty = tap / 3, tx = tap % 3;
+          if (a.mode == HELM_CONV_S2) {
+            const int sy = ty == 0 ? -1 : 0, py = ty == 1 ? 0 : 1;
+            const int sx = tx == 0 ? -1 : 0, px = tx == 1 ? 0 : 1;
+            ph = py * 2 + px;
+            row = (sy + 1) * a.Po + (sx + 1);
+          } else {
+            row = ty * a.Po + tx;
+          }
+        }
+#pragma unroll
+        for (int kc = 0; kc < CS / 16; ++kc) {
+          const uint32_t aaddr = sA_u + static_cast<uint32_t>(((ph * G + 2 * kc) * L + row) * 16);
+          const uint64_t ad = tc::sdesc(aaddr, lboA, 128);
+#pragma unroll
+          for (int nh = 0; nh < Cfg::NSPLIT; ++nh) {
+            const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT + nh * Cfg::NH) * 16);
+            const uint64_t bd = tc::sdesc(baddr, COUT * 16, 128);
+            tc::mma_bf16(tmem + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
+          }
+          ++kstep;
+        }
+      }
+      tc::commit(bar);
+    }
+    ok = mbar_wait_bounded(bar, phase, HELM_DEVERR_MMA_WAIT);
+    phase ^= 1;
+    tc::fence_after_sync();
+    // ---- epilogue: thread tid <-> TMEM lane tid <-> pixel q0 + tid ----
+    const int q = q0 + tid;
+    const int y = q / a.Po, x = q % a.Po;
+    const bool valid = ok && y < a.Ho && x < a.Wo;
+    const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
+    const long pix2 = a.add2_bcast ? static_cast<long>(y) * a.Wo + x : pix;
+#pragma unroll 1
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      if (!valid) continue;
+      if (a.yraw) {
+        float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+      if (a.y) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
+          v[i] = a.act ? tc::softplus(t) : t;
+        }
+        if (a.add1) {
+          const uint4* p = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint4 u = p[h];
+            const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+          }
+        }
+        if (a.add2) {
+          const uint4* p = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint4 u = p[h];
+            const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+          }
+        }
+        uint4 o[2];
+        bf16* ob = reinterpret_cast<bf16*>(o);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) ob[i] = __float2bfloat16_rn(v[i]);
+        uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
+        dst[0] = o[0];
+        dst[1] = o[1];
+      }
+    }
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok) != 0;  // uniform: a timed-out wait stops every thread
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, Cfg::NCOLS);
+}
+
+// ---- weight packing: FP32 master layout -> BF16 [taps][G][COUT][8] ------------------
+// conv (mode S1/S2): w[co][ci][ky][kx]; transposed (T1/T2): w[ci][co][ky][kx], flipped;
+// 1x1: w[co][ci].
+__global__ void k_pack_weights(const float* __restrict__ w, int Ci, int Co, int CS, int taps, int transposed,
+                               bf16* __restrict__ out) {
+  const int G = CS / 8;
+  const long total = static_cast<long>(taps) * G * Co * 8;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int e = static_cast<int>(i % 8);
+    const int co = static_cast<int>((i / 8) % Co);
+    const int g = static_cast<int>((i / (8L * Co)) % G);
+    const int tap = static_cast<int>(i / (8L * Co * G));
+    const int ci = 8 * g + e;
+    float v = 0.f;
+    if (ci < Ci) {
+      if (taps == 1) {
+        v = w[static_cast<long>(co) * Ci + ci];
+      } else {
+        const int ty = tap / 3, tx = tap % 3;
+        if (transposed)
+          v = w[((static_cast<long>(ci) * Co + co) * 3 + (2 - ty)) * 3 + (2 - tx)];
+        else
+          v = w[((static_cast<long>(co) * Ci + ci) * 3 + ty) * 3 + tx];
+      }
+    }
+    out[i] = __float2bfloat16_rn(v);
+  }
+}
+
+template <int CS, int COUT, int TAPS>
+int launch_t(const ConvArgs& a0, cudaStream_t st) {
+  using Cfg = ConvCfg<CS, COUT, TAPS>;
+  ConvArgs a = a0;
+  const int nph = a.mode == HELM_CONV_S2 ? 4 : 1;
+  const size_t smem = Cfg::BBYTES + static_cast<size_t>(nph) * Cfg::G * a.L * 16 + 2 * COUT * 4 + 64;
+  if (smem > 227 * 1024) {
+    helm::set_error("conv: shared memory %zu bytes exceeds the per-CTA limit (grid row too wide)", smem);
+    return HELM_ESHAPE;
+  }
+  static int nsm = 0;
+  static bool attr = false;
+  if (!attr) {
+    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   227 * 1024));
+    int dev;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    attr = true;
+  }
+  int per_sm = 0;
+  HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CS, COUT, TAPS>, 128, smem));
+  per_sm = std::max(1, std::min(per_sm, 512 / Cfg::NCOLS));
+  const int grid = std::max(1, std::min(a.ntiles, nsm * per_sm));
+  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS><<<grid, 128, smem, st>>>(a));
+  HELM_CHECK_LAUNCH("k_conv_tc");
+  return HELM_OK;
+}
+
+}  // namespace
+
+namespace helm {
+
+int pack_conv_weights(const float* w, int Ci, int Co, int taps, int transposed, bf16* out, cudaStream_t st) {
+  const int CS = conv_cs(Ci);
+  const long total = static_cast<long>(taps) * (CS / 8) * Co * 8;
+  HELM_LAUNCH("k_pack_weights", st,
+              k_pack_weights<<<std::min<long>(div_up(total, 256), 2048), 256, 0, st>>>(w, Ci, Co, CS, taps,
+                                                                                        transposed, out));
+  HELM_CHECK_LAUNCH("k_pack_weights");
+  return HELM_OK;
+}
+
+int conv_tc(const ConvLaunch& c, cudaStream_t st) {
+  ConvArgs a;
+  a.x = c.x;
+  a.B = c.B;
+  a.Hi = c.Hi;
+  a.Wi = c.Wi;
+  a.Cg = c.Ci;
+  a.mode = c.mode;
+  a.wpk = c.wpk;
+  a.scale = c.scale;
+  a.shift = c.shift;
+  a.act = c.act;
+  a.add1 = c.add1;
+  a.add2 = c.add2;
+  a.add2_bcast = c.add2_bcast;
+  a.y = c.y;
+  a.yraw = c.yraw;
+  const int taps = c.taps;
+  if (taps == 1) {
+    a.Ho = c.Hi;
+    a.Wo = c.Wi;
+    a.Po = a.Wo;
+  } else if (c.mode == HELM_CONV_S2) {
+    if ((c.Hi & 1) || (c.Wi & 1)) {
+      set_error("conv: stride-2 input must have even size");
+      return HELM_ESHAPE;
+    }
+    a.Ho = c.Hi / 2;
+    a.Wo = c.Wi / 2;
+    a.Po = a.Wo + 1;
+  } else if (c.mode == HELM_CONV_T2) {
+    a.Ho = 2 * c.Hi;
+    a.Wo = 2 * c.Wi;
+    a.Po = a.Wo + 1;
+  } else {
+    a.Ho = c.Hi;
+    a.Wo = c.Wi;
+    a.Po = a.Wo + 1;
+  }
+  a.L = taps == 1 ? 128 : (c.mode == HELM_CONV_S2 ? 128 + a.Po + 1 : 128 + 2 * a.Po + 2);
+  a.tiles_per_img = div_up(static_cast<long>(a.Ho) * a.Po, 128);
+  a.ntiles = a.tiles_per_img * a.B;
+  const int CS = conv_cs(c.Ci);
+#define HELM_CONV_CASE(cs, co, tp) \
+  if (CS == cs && c.Co == co && taps == tp) return launch_t<cs, co, tp>(a, st);
+  HELM_CONV_CASE(16, 16, 9)
+  HELM_CONV_CASE(16, 32, 9)
+  HELM_CONV_CASE(32, 32, 9)
+  HELM_CONV_CASE(32, 16, 9)
+  HELM_CONV_CASE(32, 64, 9)
+  HELM_CONV_CASE(64, 64, 9)
+  HELM_CONV_CASE(64, 32, 9)
+  HELM_CONV_CASE(16, 96, 1)
+  HELM_CONV_CASE(96, 16, 1)
+  HELM_CONV_CASE(32, 192, 1)
+  HELM_CONV_CASE(192, 32, 1)
+  HELM_CONV_CASE(64, 384, 1)
+  HELM_CONV_CASE(384, 64, 1)
+#undef HELM_CONV_CASE
+  set_error("conv: no tensor-core kernel for Cin=%d Cout=%d taps=%d", c.Ci, c.Co, taps);
+  return HELM_EINVAL;
+}
+
+}  // namespace helm
+
+extern "C" int helm_conv_bf16(const void* x, int batch, int hi, int wi, int cin, const float* w, int cout, int taps,
+                              int mode, const float* scale, const float* shift, int act, const void* add1,
+                              const void* add2, int add2_bcast, void* y, float* yraw, void* ws, size_t ws_bytes,
+                              void* stream) {
+  using namespace helm;
+  if (!x || !w || batch <= 0 || hi <= 0 || wi <= 0 || cin <= 0 || cout <= 0 || (taps != 1 && taps != 9) ||
+      (!y && !yraw) || mode < 0 || mode > HELM_CONV_T1) {
+    set_error("helm_conv_bf16: invalid argument");
+    return HELM_EINVAL;
+  }
+  if ((cin > 2 && cin % 8) || cout % 16) {
+    set_error("helm_conv_bf16: cin must be <= 2 or a multiple of 8, cout a multiple of 16");
+    return HELM_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve cv(ws, ws_bytes);
+  bf16* wpk = cv.take<bf16>(static_cast<size_t>(taps) * conv_cs(cin) * cout);
+  if (cv.overflow || !ws) {
+    set_error("helm_conv_bf16: workspace too small (need %zu bytes)", cv.off);
+    return HELM_EWORKSPACE;
+  }
+  int rc = pack_conv_weights(w, cin, cout, taps, mode == HELM_CONV_T2 || mode == HELM_CONV_T1, wpk, st);
+  if (rc) return rc;
+  ConvLaunch c;
+  c.x = static_cast<const bf16*>(x);
+  c.B = batch;
+  c.Hi = hi;
+  c.Wi = wi;
+  c.Ci = cin;
+  c.Co = cout;
+  c.taps = taps;
+  c.mode = mode == HELM_CONV_T1 ? HELM_CONV_S1 : mode;
+  c.wpk = wpk;
+  c.scale = scale;
+  c.shift = shift;
+  c.act = act;
+  c.add1 = static_cast<const bf16*>(add1);
+  c.add2 = static_cast<const bf16*>(add2);
+  c.add2_bcast = add2_bcast;
+  c.y = static_cast<bf16*>(y);
+  c.yraw = yraw;
+  return conv_tc(c, st);
+}

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) k_prolong_smooth(const __grid_constant__ 
                                                         const float2* __restrict__ mass,
                                                         const float2* __restrict__ dinv, float2* __restrict__ z,
                                                         int nx, int ny, const int* __restrict__ active,
-                                                        const float* __restrict__ rscale) {
+                                                        const float* __restrict__ rscale,
+                                                        const float2* __restrict__ zadd) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   __shared__ alignas(128) float2 R[PR_H * PR_W];
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(256) k_prolong_smooth(const __grid_constant__ 
       float2 su = cmul(make_float2(4.f - m.x, -m.y), U[i]);
       su = csub(su, cadd(cadd(U[i - PR_W], U[i + PR_W]), cadd(U[i - 1], U[i + 1])));
       out[q] = cadd(U[i], cmul(dinv[gi + q], csub(R[i], su)));
+      if (zadd) out[q] = cadd(out[q], zadd[b * plane + gi + q]);
     }
     *reinterpret_cast<float4*>(z + b * plane + gi) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
   }
@@ -617,7 +619,7 @@ void carve_vcycle(Carve& c, const helm_problem* p, int batch, VcycleScratch* s) 
 }
 
 int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, const VcycleScratch& s,
-                  const int* active, const float* rscale, cudaStream_t st) {
+                  const int* active, const float* rscale, cudaStream_t st, const float2* zadd) {
   const int L = p->mg.levels;
   int rc;
   for (int l = 0; l + 1 < L; ++l) {
@@ -659,7 +661,7 @@ int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, 
     if ((rc = make_c64_map(&me, s.ec[l + 1], p->lnx[l + 1], p->lny[l + 1], batch, PE_W, PE_H))) return rc;
     dim3 grid(div_up(p->lnx[l], PS_TW), div_up(p->lny[l], PS_TH), batch);
     HELM_LAUNCH("k_prolong_smooth", st, k_prolong_smooth<<<grid, 256, 0, st>>>(mr, me, p->massSL[l], p->dinvSL[l], zout, p->lnx[l], p->lny[l], active,
-                                           l == 0 ? rscale : nullptr));
+                                           l == 0 ? rscale : nullptr, l == 0 ? zadd : nullptr));
     HELM_CHECK_LAUNCH("k_prolong_smooth");
   }
   return HELM_OK;

@@ -1,0 +1,114 @@
+"""GPU parity of the encoder-solver network against the FP64 oracle (through the C ABI).
+
+The GPU keeps activations and 3x3/1x1 conv weights in BF16 (FP32 accumulation);
+depthwise, projection, BN and the implicit layer compute in FP32.  Each of ~30
+layers rounds its output to BF16 (relative 2^-9 per element on average), so the
+network output carries a relative error of order sqrt(30) * 2^-9 * (gain of the
+later layers): measured ~0.5-1%, bound 4% in the 2-norm.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import cnn as ocnn
+from oracle import helmholtz as ohz
+from oracle import implicit as oimp
+from oracle import multigrid as omg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2306_17486_gb300 as h
+    return h
+
+
+def _bf(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+
+
+def _random_net(seed):
+    P = synth.random_params(ocnn.param_spec(16), seed=seed, bn_jitter=0.2)
+    rng = np.random.default_rng(seed + 1)
+    K = P["s.imp.K"]
+    P["s.imp.K"] = K + 0.1 * rng.standard_normal(K.shape)
+    running = {n: (0.1 * rng.standard_normal(c), rng.uniform(0.5, 2.0, c)) for n, c in ocnn.bn_names(16)}
+    return P, running
+
+
+def test_parameter_table_matches_oracle(helm):
+    net = helm.Cnn()
+    spec = ocnn.param_spec(16)
+    assert [(n, tuple(s)) for n, s, *_ in spec] == [(n, s) for n, s, _ in net.spec]
+    assert [n for n, _ in ocnn.bn_names(16)] == [n for n, _, _ in net.bn]
+    assert net.nparams == ocnn.num_params(16)
+
+
+@pytest.mark.parametrize("m", [4, 8, 16, 36])
+def test_green_function_matches_oracle(helm, m):
+    P, running = _random_net(3)
+    net = helm.Cnn()
+    net.load_dict(P)
+    g = net.ghat(m).cpu().numpy()
+    ref = ocnn.build_ghat(P, m)
+    err = np.abs(g - ref).max() / np.abs(ref).max()
+    assert err < 2e-5, err
+
+
+@pytest.mark.parametrize("I,skip_threshold,B", [(64, 512, 2), (128, 64, 2), (96, 512, 1)])
+def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
+    P, running = _random_net(5)
+    # the GPU's conv weights are BF16: give the oracle the same rounded values
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn(skip_threshold=skip_threshold)
+    net.load_dict(Pq)
+    net.load_running(running)
+    abl = I // 8
+    kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 7).astype(np.float32).astype(np.float64)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    r = synth.random_complex((B, I, I), 9).astype(np.complex64).astype(np.complex128)
+    e = net.apply(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    on = ocnn.Network(Pq, running, c0=16)
+    ref, _ = on.forward(r, ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64)),
+                        train=False, skip=I < skip_threshold)
+    for i in range(B):
+        err = np.linalg.norm(e[i] - ref[i]) / np.linalg.norm(ref[i])
+        assert err < 4e-2, (i, err)
+    # scale equivariance holds exactly up to rounding: e(3r) = 3 e(r)
+    e3 = net.apply(p, torch.tensor(3 * r, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    assert np.linalg.norm(e3 - 3 * e) <= 1e-5 * np.linalg.norm(3 * e)
+
+
+def test_composed_preconditioner_matches_oracle(helm):
+    I, abl, B = 64, 8, 2
+    P, running = _random_net(11)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn()
+    net.load_dict(Pq)
+    net.load_running(running)
+    kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 2).astype(np.float32).astype(np.float64)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    r = synth.random_complex((B, I, I), 4).astype(np.complex64).astype(np.complex128)
+    z = net.precond(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    mg = omg.SLMultigrid(op, 3)
+    on = ocnn.Network(Pq, running, c0=16)
+    kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
+    from oracle.training import composed_preconditioner
+    M = composed_preconditioner(op, on, kf, mg)
+    for i in range(B):
+        ref = M(r[i])
+        err = np.linalg.norm(z[i] - ref) / np.linalg.norm(ref)
+        assert err < 4e-2, err
