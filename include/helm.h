@@ -241,6 +241,28 @@ int helm_cnn_set_problem(helm_cnn* c, const helm_problem* p, void* ws, size_t ws
 int helm_cnn_apply(const helm_problem* p, helm_cnn* c, const void* r, void* e, int batch, int train, void* ws,
                    size_t ws_bytes, void* stream);
 
+/* Bytes of the training workspace for helm_cnn_apply(train = 1) followed by
+ * helm_cnn_precond_backward at this batch size (activations, raw BN inputs, statistics,
+ * gradients of every activation, reduction partials). */
+int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int batch, size_t* bytes);
+
+/* Backward of the last training-mode helm_cnn_apply that used the same workspace:
+ * grad_e (complex64 [batch][N][N], dLoss/dRe e + i dLoss/dIm e) -> grad_params (FP32,
+ * parameter layout, overwritten).  Covers the solver and the encoder (the encodings
+ * receive the batch sum of their gradients); the V-cycle is not differentiated. */
+int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* grad_e, float* grad_params, int batch,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. (16): loss = (1/batch) sum |e_pred - e_true|^2 over n complex entries (all
+ * batch items), written as float64 to loss_dev; grad (nullable, complex64 like e_pred)
+ * receives 2 (e_pred - e_true) / batch.  ws: >= 4096 bytes of device scratch. */
+int helm_mse_loss(const void* e_pred, const void* e_true, long n, int batch, double* loss_dev, void* grad, void* ws,
+                  void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n FP32 parameters, moments m, v. */
+int helm_adam_step(float* params, const float* grads, float* m, float* v, long n, double lr, double beta1,
+                   double beta2, double eps, int step, void* stream);
+
 /* Copy G_hat (Eq. 15, after crop and DFT) for coarsest size m to out_dev, complex64
  * [nk][2m][2m]; builds it if needed. */
 int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream);

@@ -306,3 +306,75 @@ class Cnn:
         check(lib().helm_cnn_precond_apply(p.handle, self.handle, _ptr(r), _ptr(z), B, _ptr(ws), ws.numel(),
                                            _stream()), "helm_cnn_precond_apply")
         return z
+
+    # ---- training ---------------------------------------------------------------
+    def train_workspace(self, p: Problem, batch: int) -> torch.Tensor:
+        n = C.c_size_t()
+        check(lib().helm_cnn_train_workspace_size(p.handle, self.handle, batch, C.byref(n)), "train_workspace_size")
+        ws = getattr(self, "_tws", None)
+        if ws is None or ws.numel() < n.value:
+            self._tws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        return self._tws
+
+    def forward_train(self, p: Problem, r: torch.Tensor) -> torch.Tensor:
+        """Training-mode forward (batch-statistics BN; saves activations for backward)."""
+        _need(r, torch.complex64, "r")
+        B = r.shape[0]
+        ws = self.train_workspace(p, B)
+        e = torch.empty_like(r)
+        check(lib().helm_cnn_apply(p.handle, self.handle, _ptr(r), _ptr(e), B, 1, _ptr(ws), ws.numel(), _stream()),
+              "helm_cnn_apply(train)")
+        return e
+
+    def backward(self, p: Problem, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None) -> torch.Tensor:
+        _need(grad_e, torch.complex64, "grad_e")
+        B = grad_e.shape[0]
+        g = torch.empty_like(self.params) if grad_params is None else grad_params
+        ws = self.train_workspace(p, B)
+        check(lib().helm_cnn_precond_backward(p.handle, self.handle, _ptr(grad_e), _ptr(g), B, _ptr(ws), ws.numel(),
+                                              _stream()), "helm_cnn_precond_backward")
+        return g
+
+
+def mse_loss(e_pred: torch.Tensor, e_true: torch.Tensor, grad: bool = True):
+    """Eq. (16) on the device: (loss tensor (float64, shape [1]), gradient or None)."""
+    _need(e_pred, torch.complex64, "e_pred")
+    _need(e_true, torch.complex64, "e_true")
+    B = e_pred.shape[0]
+    loss = torch.empty(1, dtype=torch.float64, device=e_pred.device)
+    g = torch.empty_like(e_pred) if grad else None
+    ws = torch.empty(8192, dtype=torch.uint8, device=e_pred.device)
+    check(lib().helm_mse_loss(_ptr(e_pred), _ptr(e_true), e_pred.numel(), B, _ptr(loss), _ptr(g), _ptr(ws),
+                              _stream()), "helm_mse_loss")
+    return loss, g
+
+
+class Adam:
+    """Adam on the device (helm_adam_step), FP32 moments."""
+
+    def __init__(self, params: torch.Tensor, lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+        self.p = params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.lr, self.b1, self.b2, self.eps = lr, betas[0], betas[1], eps
+        self.t = 0
+
+    def step(self, grads: torch.Tensor):
+        self.t += 1
+        check(lib().helm_adam_step(_ptr(self.p), _ptr(grads), _ptr(self.m), _ptr(self.v), self.p.numel(), self.lr,
+                                   self.b1, self.b2, self.eps, self.t, _stream()), "helm_adam_step")
+
+
+class CnnFunction(torch.autograd.Function):
+    """torch.autograd wrapper around the training forward / backward kernels:
+    e = CnnFunction.apply(params, r, net, problem).  Gradients flow to `params`."""
+
+    @staticmethod
+    def forward(ctx, params, r, net, problem):
+        ctx.net, ctx.problem = net, problem
+        return net.forward_train(problem, r)
+
+    @staticmethod
+    def backward(ctx, grad_e):
+        g = ctx.net.backward(ctx.problem, grad_e.contiguous())
+        return g, None, None, None

@@ -83,6 +83,8 @@ void build_params(helm_cnn* c) {
   add_param(c, "s.proj.b", {2});
 }
 
+}  // namespace
+
 size_t packed_elems(const helm_cnn* c, const ParamInfo& pi) {
   (void)c;
   if (pi.shape.size() == 4) {  // 3x3 conv [co][ci][3][3] or transposed [ci][co][3][3]
@@ -95,8 +97,6 @@ size_t packed_elems(const helm_cnn* c, const ParamInfo& pi) {
     return static_cast<size_t>(conv_cs(pi.shape[1])) * pi.shape[0];
   return 0;
 }
-
-}  // namespace
 
 int skip_for(const helm_cnn* c, int I) { return I < c->desc.skip_threshold ? 1 : 0; }
 
@@ -307,7 +307,7 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
   return HELM_OK;
 }
 
-static size_t wpk_offset(const helm_cnn* c, int param) {
+size_t wpk_offset(const helm_cnn* c, int param) {
   size_t off = 0;
   for (int i = 0; i < param; ++i) off += packed_elems(c, c->params[i]);
   return off;

@@ -112,3 +112,68 @@ def test_composed_preconditioner_matches_oracle(helm):
         ref = M(r[i])
         err = np.linalg.norm(z[i] - ref) / np.linalg.norm(ref)
         assert err < 4e-2, err
+
+
+@pytest.mark.parametrize("I,skip_threshold", [(64, 512), (128, 64)])
+def test_training_forward_and_gradients_match_oracle(helm, I, skip_threshold):
+    """Batch-statistics forward and every parameter gradient vs the oracle's
+    hand-written reverse mode (the oracle's gradients are pinned by finite differences).
+    BF16 activations in the GPU forward leave gradient errors of a few percent; per
+    tensor the relative 2-norm error must stay below 10% and the cosine above 0.99."""
+    B = 2
+    P, running = _random_net(21)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn(skip_threshold=skip_threshold)
+    net.load_dict(Pq)
+    abl = I // 8
+    kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 3).astype(np.float32).astype(np.float64)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, gamma0=0.05, levels=3)
+    r = synth.random_complex((B, I, I), 5)
+    r /= np.sqrt((np.abs(r) ** 2).sum(axis=(1, 2)))[:, None, None]
+    r = r.astype(np.complex64).astype(np.complex128)
+    et = 0.3 * synth.random_complex((B, I, I), 6) / I
+    et = et.astype(np.complex64).astype(np.complex128)
+    rg = torch.tensor(r, dtype=torch.complex64, device="cuda")
+    eg = net.forward_train(p, rg)
+    loss, ge = helm.mse_loss(eg, torch.tensor(et, dtype=torch.complex64, device="cuda"))
+    grads = net.to_dict(net.backward(p, ge))
+    op = ohz.Problem(kappa, abl, omega_h=oh, gamma0=0.05)
+    on = ocnn.Network(Pq, None, c0=16)
+    kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
+    from oracle.training import mse_loss as omse
+    e_ref, tp = on.forward(r, kf, train=True, skip=I < skip_threshold, record=True)
+    L, g_e = omse(e_ref, et)
+    ref = on.backward(tp, g_e)
+    assert np.linalg.norm(eg.cpu().numpy() - e_ref) <= 4e-2 * np.linalg.norm(e_ref)
+    assert abs(loss.item() - L) <= 5e-2 * L
+    worst = []
+    for name in ref:
+        a, b = grads[name], ref[name]
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        cos = float((a * b).sum() / (np.linalg.norm(a) * nb + 1e-300))
+        worst.append((rel, name, cos))
+    worst.sort(reverse=True)
+    assert worst[0][0] < 0.1, worst[:5]
+    assert min(w[2] for w in worst) > 0.99, worst[:5]
+    # BN running statistics moved by momentum 0.1 toward the batch statistics
+    rs = net.running_dict()
+    assert not np.allclose(rs["s.l1.bn"][0], 0.0)
+
+
+def test_adam_matches_oracle(helm):
+    from oracle.training import adam_step
+    rng = np.random.default_rng(3)
+    p0 = rng.standard_normal(1000)
+    pg = torch.tensor(p0, dtype=torch.float32, device="cuda")
+    opt = helm.Adam(pg, lr=1e-3)
+    pr = {"w": p0.astype(np.float32).astype(np.float64)}
+    state = {}
+    for k in range(5):
+        g = rng.standard_normal(1000)
+        opt.step(torch.tensor(g, dtype=torch.float32, device="cuda"))
+        adam_step(pr, {"w": g.astype(np.float32).astype(np.float64)}, state, lr=1e-3)
+    assert np.allclose(pg.cpu().numpy(), pr["w"], atol=1e-6, rtol=1e-5)
