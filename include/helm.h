@@ -160,7 +160,7 @@ void helm_fgmres_opts_default(helm_fgmres_opts* o);
  * b: complex64 [batch][ny][nx]; x: complex128 [batch][ny][nx], in: initial guess,
  * out: solution (accumulated in FP64; the Krylov vectors are FP32).
  * cnn: NULL for the SL V-cycle preconditioner, else the composed preconditioner
- *   z = e + V(r - A e), e = ||r|| Net(r / ||r||)  (Section 4.1), with the warm-up cycle.
+ *   z = e + V(r - A e), e = s Net(r / s), s = RMS(r)  (Section 4.1), with the warm-up cycle.
  * maxit_dev: nullable device int [batch] per-RHS caps (min with opts->maxit).
  * stats_dev: device helm_fgmres_stats [batch] written at exit.
  * The call synchronises `stream` once per restart cycle to test for completion.
@@ -233,8 +233,8 @@ int helm_cnn_get_running(helm_cnn* c, float* out_dev, void* stream);
  * iteration).  Needed again after helm_cnn_set_params. */
 int helm_cnn_set_problem(helm_cnn* c, const helm_problem* p, void* ws, size_t ws_bytes, void* stream);
 
-/* e = ||r|| Net(r / ||r||) (Eq. 16's SolverNet with the residual normalisation of
- * this library), r, e complex64 [batch][N][N].  train = 0: evaluation-mode BN with the
+/* e = s Net(r / s), s = RMS of r over the grid (Eq. 16's SolverNet with the residual
+ * normalisation of this library), r, e complex64 [batch][N][N].  train = 0: evaluation-mode BN with the
  * cached encodings.  train = 1: batch-statistics BN, encoder run on p in training mode
  * inside the call, activations saved in `ws` for helm_cnn_precond_backward, running
  * statistics updated (momentum 0.1). */
@@ -267,9 +267,21 @@ int helm_adam_step(float* params, const float* grads, float* m, float* v, long n
  * [nk][2m][2m]; builds it if needed. */
 int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream);
 
-/* The composed preconditioner of Section 4.1: z = e + V(r - A e), e = ||r|| Net(r/||r||). */
+/* The composed preconditioner of Section 4.1: z = e + V(r - A e), e = s Net(r/s), s = RMS(r). */
 int helm_cnn_precond_apply(const helm_problem* p, helm_cnn* c, const void* r, void* z, int batch, void* ws,
                            size_t ws_bytes, void* stream);
+
+/*
+ * Training pairs of Section 4.3, Eq. (17): for random x (complex64 [batch][N][N]),
+ * b = A x (with the problem's gamma, 0.05 in training), x_tilde = FGMRES with the SL
+ * V-cycle from x0 = 0 run for exactly iters_dev[i] steps (1 <= iters <= max_iters <= 32,
+ * one cycle), e = x - x_tilde and r = b - A x_tilde (FP64 evaluation), written as
+ * complex64; normalise = 1 scales both by 1/RMS(r_i) (RMS over the grid).  Workspace:
+ * helm_datagen_workspace_size().
+ */
+int helm_datagen_pairs(const helm_problem* p, const void* x, const int* iters_dev, void* e, void* r, int batch,
+                       int max_iters, int normalise, void* ws, size_t ws_bytes, void* stream);
+int helm_datagen_workspace_size(const helm_problem* p, int batch, int max_iters, size_t* bytes);
 
 /* Read and clear the device error word (HELM_DEVERR_* bits) of the current device. */
 int helm_device_errors(unsigned int* flags);

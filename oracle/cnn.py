@@ -9,7 +9,7 @@ Architecture (c0 = 16, expansion t = 6; readings where the paper is silent):
     followed by BatchNorm + softplus (Fig. 1: every convolutional block is);
     outputs enc1 = c0 x I/2, enc2 = 2c0 x I/4, enc3 = 4c0 x I/8.
   Solver (Section 5.3, 4.4):
-    r -> s = ||r||, fixed full-weighting R of r/s to I/2 (2 channels Re, Im)
+    r -> s = RMS(r) over the grid, fixed full-weighting R of r/s to I/2 (2 channels)
     level 1: 3x3 conv 2->c0 (stride 1) + BN + softplus, + enc1, inverted bottleneck
     level 2: 3x3 stride-2 conv c0->2c0 + BN + softplus, + enc2, inverted bottleneck
     level 3: 3x3 stride-2 conv 2c0->4c0 + BN + softplus, + enc3, inverted bottleneck
@@ -427,14 +427,17 @@ class Network:
 
     def forward(self, r: np.ndarray, kfeat: np.ndarray, train: bool = False,
                 skip: bool | None = None, record: bool = False):
-        """e = ||r|| * Net(r / ||r||) for a batch r [B, I, I] complex (reading A10).
+        """e = s * Net(r / s), s = RMS of r over the grid, for a batch r [B, I, I] complex
+        (reading A10).
 
         Returns (e, tape, scale); the tape's backward accumulates parameter
         gradients in tape.grads given the complex gradient of the loss w.r.t. e.
         """
         B, I, _ = r.shape
         skip = skip_last_down(I) if skip is None else skip
-        s = np.sqrt((np.abs(r) ** 2).reshape(B, -1).sum(axis=1))
+        # reading A10: s is the residual's RMS over the grid, so the network sees O(1)
+        # values at every grid size (the multiscale setting of Section 4.3)
+        s = np.sqrt((np.abs(r) ** 2).reshape(B, -1).mean(axis=1))
         s_safe = np.where(s > 0, s, 1.0)
         rn = r / s_safe[:, None, None]
         rc = restrict(rn)                                     # fixed R to I/2

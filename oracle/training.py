@@ -26,8 +26,9 @@ def generate_pairs(problem, vcycle, x: np.ndarray, iters: np.ndarray):
 
 
 def normalise_pairs(e: np.ndarray, r: np.ndarray):
-    """Reading A10: training pairs are scaled by 1/||r_i|| (both e and r)."""
-    s = np.sqrt((np.abs(r) ** 2).reshape(r.shape[0], -1).sum(axis=1))
+    """Reading A10: training pairs are scaled by 1/s_i (both e and r), s_i the RMS of
+    r_i over the grid."""
+    s = np.sqrt((np.abs(r) ** 2).reshape(r.shape[0], -1).mean(axis=1))
     return e / s[:, None, None], r / s[:, None, None]
 
 

@@ -277,6 +277,14 @@ class Cnn:
         v = self.running.cpu().numpy().astype(np.float64)
         return {name: (v[ro:ro + c].copy(), v[ro + c:ro + 2 * c].copy()) for name, c, ro in self.bn}
 
+    def running_dict_flat(self) -> np.ndarray:
+        check(lib().helm_cnn_get_running(self.handle, _ptr(self.running), _stream()), "get_running")
+        return self.running.cpu().numpy().copy()
+
+    def load_running_flat(self, flat):
+        self.running.copy_(torch.as_tensor(np.asarray(flat, dtype=np.float32)))
+        check(lib().helm_cnn_set_running(self.handle, _ptr(self.running), _stream()), "set_running")
+
     def ghat(self, m: int) -> torch.Tensor:
         nk = dict((n, s) for n, s, _ in self.spec)["s.imp.K"][1]
         out = torch.empty((nk, 2 * m, 2 * m), dtype=torch.complex64, device=self.device)
@@ -378,3 +386,21 @@ class CnnFunction(torch.autograd.Function):
     def backward(ctx, grad_e):
         g = ctx.net.backward(ctx.problem, grad_e.contiguous())
         return g, None, None, None
+
+
+def datagen_pairs(p: Problem, x: torch.Tensor, iters: torch.Tensor, max_iters: int = 20, normalise: bool = True):
+    """Eq. (17) on the device: (e, r) complex64 for random x [B, N, N] (complex64) and
+    per-sample FGMRES iteration counts `iters` (int32 CUDA tensor)."""
+    _need(x, torch.complex64, "x")
+    _need(iters, torch.int32, "iters")
+    B = x.shape[0]
+    n = C.c_size_t()
+    check(lib().helm_datagen_workspace_size(p.handle, B, max_iters, C.byref(n)), "datagen_workspace_size")
+    ws = getattr(p, "_dws", None)
+    if ws is None or ws.numel() < n.value:
+        p._dws = ws = torch.empty(n.value, dtype=torch.uint8, device=x.device)
+    e = torch.empty_like(x)
+    r = torch.empty_like(x)
+    check(lib().helm_datagen_pairs(p.handle, _ptr(x), _ptr(iters), _ptr(e), _ptr(r), B, max_iters, int(normalise),
+                                   _ptr(ws), ws.numel(), _stream()), "helm_datagen_pairs")
+    return e, r

@@ -49,6 +49,8 @@ PROTOS = {
     "helm_slmg_vcycle": (i32, [vp, vp, vp, i32, vp, sz, vp]),
     "helm_fgmres_opts_default": (None, [C.POINTER(FgmresOpts)]),
     "helm_fgmres_solve": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, vp, vp, sz, vp]),
+    "helm_datagen_pairs": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]),
+    "helm_datagen_workspace_size": (i32, [vp, i32, i32, C.POINTER(sz)]),
     "helm_device_errors": (i32, [C.POINTER(C.c_uint)]),
     "helm_last_error_string": (C.c_char_p, []),
     "helm_version": (C.c_char_p, []),

@@ -21,7 +21,7 @@ __global__ void k_kfeat(const float* __restrict__ kappa, const float* __restrict
   }
 }
 
-// ---- ||r_b||^2 partial sums and the final scale s_b = ||r_b|| ----------------------
+// ---- ||r_b||^2 partial sums and the input scale s_b = RMS(r_b) -------------------
 __global__ void k_norm_partial(const float2* __restrict__ r, long n, int nblk, double* __restrict__ part) {
   const int b = blockIdx.y;
   const long chunk = (n + nblk - 1) / nblk;
@@ -42,18 +42,20 @@ __global__ void k_norm_partial(const float2* __restrict__ r, long n, int nblk, d
   }
 }
 
-__global__ void k_norm_final(const double* __restrict__ part, int nblk, int B, float* __restrict__ s,
+// s_b = RMS of r_b over the grid (the network's input scale, reading A10)
+__global__ void k_norm_final(const double* __restrict__ part, int nblk, int B, long n, float* __restrict__ s,
                              float* __restrict__ inv) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   double t = 0;
   for (int i = 0; i < nblk; ++i) t += part[static_cast<long>(b) * nblk + i];
-  const double v = sqrt(t);
+  const double v = sqrt(t / static_cast<double>(n));
   s[b] = static_cast<float>(v);
   inv[b] = v > 0.0 ? static_cast<float>(1.0 / v) : 0.f;
 }
 
 // x0[b][J][K][0..1] = (Re, Im) of I_h^H (r_b / s_b): full weighting, zero padding
+// (s_b the RMS of r_b)
 __global__ void k_prep_restrict(const float2* __restrict__ r, int N, int B, const float* __restrict__ inv,
                                 bf16* __restrict__ x0) {
   const int Nc = N / 2;
@@ -383,7 +385,7 @@ int launch_prep(const float2* r, int N, int B, double* part, float* s, float* in
   const long n = static_cast<long>(N) * N;
   const int nblk = std::max(1, std::min(256, div_up(n, 4096)));
   HELM_LAUNCH("k_norm_partial", st, k_norm_partial<<<dim3(nblk, B), 256, 0, st>>>(r, n, nblk, part));
-  HELM_LAUNCH("k_norm_final", st, k_norm_final<<<div_up(B, 64), 64, 0, st>>>(part, nblk, B, s, inv));
+  HELM_LAUNCH("k_norm_final", st, k_norm_final<<<div_up(B, 64), 64, 0, st>>>(part, nblk, B, n, s, inv));
   HELM_LAUNCH("k_prep_restrict", st,
               k_prep_restrict<<<grid_for(static_cast<long>(B) * (N / 2) * (N / 2)), 256, 0, st>>>(r, N, B, inv, x0));
   HELM_CHECK_LAUNCH("prep");

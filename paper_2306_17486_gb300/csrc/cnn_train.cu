@@ -28,22 +28,37 @@ __device__ __forceinline__ float spf(float x) { return fmaxf(x, 0.f) + log1pf(__
 int gridn(long n, int t = 256) { return static_cast<int>(std::min<long>(div_up(n, t), 8192)); }
 
 // ---- BatchNorm statistics: per-channel sum / sum of squares -------------------------
-constexpr int BN_CHUNK = 4096;  // pixels per block
+// pixels per reduction block: enough blocks to fill the GPU, at most kMaxChunks
+inline long bn_chunk(long P) { return std::max<long>(32, (P + 1023) / 1024); }
 
-__global__ void k_chan_sums(const float* __restrict__ z, long P, int C, double* __restrict__ part) {
-  extern __shared__ float csum[];  // [2C]
-  for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) csum[i] = 0.f;
-  __syncthreads();
-  const long p0 = static_cast<long>(blockIdx.x) * BN_CHUNK, p1 = min(p0 + BN_CHUNK, P);
-  for (long i = p0 * C + threadIdx.x; i < p1 * C; i += blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const float v = z[i];
-    atomicAdd(&csum[c], v);
-    atomicAdd(&csum[C + c], v * v);
+// block (C, k): thread (c, j) sums pixels j, j+k, ... of the chunk for channel c
+// (coalesced, no atomics, deterministic); the k partials are combined in shared memory
+__global__ void k_chan_sums(const float* __restrict__ z, long P, int C, long chunk, double* __restrict__ part) {
+  extern __shared__ double dsum[];  // [2][k][C]
+  const int c = threadIdx.x, j = threadIdx.y, k = blockDim.y;
+  const long p0 = static_cast<long>(blockIdx.x) * chunk, p1 = min(p0 + chunk, P);
+  float s1 = 0.f, s2 = 0.f;
+  for (long p = p0 + j; p < p1; p += k) {
+    const float v = z[p * C + c];
+    s1 += v;
+    s2 = fmaf(v, v, s2);
   }
+  dsum[j * C + c] = s1;
+  dsum[(k + j) * C + c] = s2;
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) part[static_cast<long>(blockIdx.x) * 2 * C + i] = csum[i];
+  if (j == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < k; ++q) {
+      a += dsum[q * C + c];
+      b += dsum[(k + q) * C + c];
+    }
+    part[static_cast<long>(blockIdx.x) * 2 * C + c] = a;
+    part[static_cast<long>(blockIdx.x) * 2 * C + C + c] = b;
+  }
 }
+
+inline dim3 chan_block(int C) { return dim3(C, std::max(1, 256 / C)); }
+inline size_t chan_smem(int C) { return 2 * sizeof(double) * C * std::max(1, 256 / C); }
 
 // mean, 1/sqrt(var + eps) (biased var); running stats: momentum 0.1, unbiased var
 __global__ void k_bn_finalize(const double* __restrict__ part, int nblk, int C, long P, float* __restrict__ mean,
@@ -86,22 +101,33 @@ __global__ void k_bn_apply(const float* __restrict__ z, long P, int C, const flo
 // dA = dY * act'(a), a = g zhat + b; per-channel sums S1 = sum dA, S2 = sum dA zhat
 __global__ void k_bn_bwd_sums(const float* __restrict__ dY, const float* __restrict__ z, long P, int C,
                               const float* __restrict__ mean, const float* __restrict__ istd,
-                              const float* __restrict__ g, const float* __restrict__ b, int act,
+                              const float* __restrict__ g, const float* __restrict__ b, int act, long chunk,
                               double* __restrict__ part) {
-  extern __shared__ float csum[];
-  for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) csum[i] = 0.f;
-  __syncthreads();
-  const long p0 = static_cast<long>(blockIdx.x) * BN_CHUNK, p1 = min(p0 + BN_CHUNK, P);
-  for (long i = p0 * C + threadIdx.x; i < p1 * C; i += blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const float zh = (z[i] - mean[c]) * istd[c];
+  extern __shared__ double dsum[];  // [2][k][C]
+  const int c = threadIdx.x, j = threadIdx.y, k = blockDim.y;
+  const long p0 = static_cast<long>(blockIdx.x) * chunk, p1 = min(p0 + chunk, P);
+  const float mu = mean[c], is = istd[c], gc = g[c], bc = b[c];
+  float s1 = 0.f, s2 = 0.f;
+  for (long p = p0 + j; p < p1; p += k) {
+    const long i = p * C + c;
+    const float zh = (z[i] - mu) * is;
     float dA = dY[i];
-    if (act) dA *= sigmoidf(g[c] * zh + b[c]);
-    atomicAdd(&csum[c], dA);
-    atomicAdd(&csum[C + c], dA * zh);
+    if (act) dA *= sigmoidf(gc * zh + bc);
+    s1 += dA;
+    s2 = fmaf(dA, zh, s2);
   }
+  dsum[j * C + c] = s1;
+  dsum[(k + j) * C + c] = s2;
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) part[static_cast<long>(blockIdx.x) * 2 * C + i] = csum[i];
+  if (j == 0) {
+    double a = 0.0, bb = 0.0;
+    for (int q = 0; q < k; ++q) {
+      a += dsum[q * C + c];
+      bb += dsum[(k + q) * C + c];
+    }
+    part[static_cast<long>(blockIdx.x) * 2 * C + c] = a;
+    part[static_cast<long>(blockIdx.x) * 2 * C + C + c] = bb;
+  }
 }
 
 __global__ void k_bn_bwd_final(const double* __restrict__ part, int nblk, int C, float* __restrict__ S,
@@ -181,17 +207,30 @@ __device__ __forceinline__ long widx(const ConvGeo& g, int ty, int tx, int co, i
   return ((static_cast<long>(co) * g.Ci + ci) * 3 + ty) * 3 + tx;
 }
 
-// dX[b][iy][ix][ci] += sum over (tap, co) with an output reading (iy, ix)
-__global__ void k_conv_dgrad(ConvGeo g, const float* __restrict__ dz, const float* __restrict__ w,
+// FP32 weights repacked as [tap][co][ci] (ci contiguous) for the input-gradient kernel
+__global__ void k_pack_dgrad_w(ConvGeo g, const float* __restrict__ w, float* __restrict__ out) {
+  const long n = static_cast<long>(g.taps) * g.Co * g.Ci;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int ci = static_cast<int>(i % g.Ci), co = static_cast<int>((i / g.Ci) % g.Co);
+    const int tap = static_cast<int>(i / (static_cast<long>(g.Ci) * g.Co));
+    const int ty = g.taps == 1 ? 1 : tap / 3, tx = g.taps == 1 ? 1 : tap % 3;
+    out[i] = w[widx(g, ty, tx, co, ci)];
+  }
+}
+
+// dX[b][iy][ix][8q..8q+7] += sum over (tap, co) of outputs reading (iy, ix); Ci % 8 == 0
+__global__ void k_conv_dgrad(ConvGeo g, const float* __restrict__ dz, const float* __restrict__ wp,
                              float* __restrict__ dX) {
-  const long total = static_cast<long>(g.B) * g.Hi * g.Wi * g.Ci;
+  const int G = g.Ci / 8;
+  const long total = static_cast<long>(g.B) * g.Hi * g.Wi * G;
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
-    const int ci = static_cast<int>(i % g.Ci);
-    const long pix = i / g.Ci;
+    const int q = static_cast<int>(i % G);
+    const long pix = i / G;
     const int ix = static_cast<int>(pix % g.Wi), iy = static_cast<int>((pix / g.Wi) % g.Hi);
     const int b = static_cast<int>(pix / (static_cast<long>(g.Wi) * g.Hi));
-    float acc = 0.f;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int tap = 0; tap < g.taps; ++tap) {
       const int ty = g.taps == 1 ? 1 : tap / 3, tx = g.taps == 1 ? 1 : tap % 3;
       const int dy = ty - 1, dx = tx - 1;
@@ -212,53 +251,106 @@ __global__ void k_conv_dgrad(ConvGeo g, const float* __restrict__ dz, const floa
       }
       if (oy < 0 || oy >= g.Ho || ox < 0 || ox >= g.Wo) continue;
       const float* dzp = dz + ((static_cast<long>(b) * g.Ho + oy) * g.Wo + ox) * g.Co;
-      for (int co = 0; co < g.Co; ++co) acc = fmaf(w[widx(g, ty, tx, co, ci)], dzp[co], acc);
+      const float* wt = wp + (static_cast<long>(tap) * g.Co) * g.Ci + 8 * q;
+      for (int co = 0; co < g.Co; ++co) {
+        const float d = dzp[co];
+        const float4 w0 = *reinterpret_cast<const float4*>(wt + static_cast<long>(co) * g.Ci);
+        const float4 w1 = *reinterpret_cast<const float4*>(wt + static_cast<long>(co) * g.Ci + 4);
+        acc[0] = fmaf(w0.x, d, acc[0]);
+        acc[1] = fmaf(w0.y, d, acc[1]);
+        acc[2] = fmaf(w0.z, d, acc[2]);
+        acc[3] = fmaf(w0.w, d, acc[3]);
+        acc[4] = fmaf(w1.x, d, acc[4]);
+        acc[5] = fmaf(w1.y, d, acc[5]);
+        acc[6] = fmaf(w1.z, d, acc[6]);
+        acc[7] = fmaf(w1.w, d, acc[7]);
+      }
     }
-    dX[i] += acc;
+    float* o = dX + pix * g.Ci + 8 * q;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o[e] += acc[e];
   }
 }
 
-// dW partials: block (tap, co-tile of 16, ci-tile of 16, pixel chunk) -> [chunk][tap][co][ci]
+// dW partials: block (tap, TCO x TCI output tile, pixel chunk) -> [chunk][tap][co][ci].
+// 256 threads, each a (TCO/16) x (TCI/16) register tile; 32 pixels staged per pass
+// (the pixel's source index is computed once per pixel, shared by the whole tile).
 constexpr int WG_PIX = 2048;
+template <int TCO, int TCI>
 __global__ void __launch_bounds__(256) k_conv_wgrad(ConvGeo g, const bf16* __restrict__ x, const float* __restrict__ dz,
                                                     float* __restrict__ part) {
+  constexpr int RO = TCO / 16, RI = TCI / 16;
+  const int nco = (g.Co + TCO - 1) / TCO;
   const int tap = blockIdx.x % g.taps;
-  const int cot = (blockIdx.x / g.taps) % ((g.Co + 15) / 16);
-  const int cit = blockIdx.x / (g.taps * ((g.Co + 15) / 16));
+  const int cot = (blockIdx.x / g.taps) % nco;
+  const int cit = blockIdx.x / (g.taps * nco);
   const int chunk = blockIdx.y;
   const int ty = g.taps == 1 ? 1 : tap / 3, tx = g.taps == 1 ? 1 : tap % 3;
-  const int co_l = threadIdx.x >> 4, ci_l = threadIdx.x & 15;
-  const int co = cot * 16 + co_l, ci = cit * 16 + ci_l;
-  __shared__ float sdz[32][16];
-  __shared__ float sx[32][17];
+  const int to = threadIdx.x >> 4, ti = threadIdx.x & 15;
+  __shared__ float sdz[32][TCO + 1];
+  __shared__ float sx[32][TCI + 1];
+  __shared__ long ssrc[32];
   const long P = static_cast<long>(g.B) * g.Ho * g.Wo;
   const long p0 = static_cast<long>(chunk) * WG_PIX, p1 = min(p0 + WG_PIX, P);
-  float acc = 0.f;
+  float acc[RO][RI];
+#pragma unroll
+  for (int a = 0; a < RO; ++a)
+#pragma unroll
+    for (int b = 0; b < RI; ++b) acc[a][b] = 0.f;
   for (long pb = p0; pb < p1; pb += 32) {
-    // stage 32 pixels x 16 co of dz and 32 pixels x 16 ci of the tap's input
-    for (int e = threadIdx.x; e < 32 * 16; e += 256) {
-      const int pl = e / 16, c = e % 16;
-      const long p = pb + pl;
-      float vz = 0.f, vx = 0.f;
+    if (threadIdx.x < 32) {
+      const long p = pb + threadIdx.x;
+      long src = -1;
       if (p < p1) {
-        const int cz = cot * 16 + c, cx = cit * 16 + c;
-        if (cz < g.Co) vz = dz[p * g.Co + cz];
         const int ox = static_cast<int>(p % g.Wo), oy = static_cast<int>((p / g.Wo) % g.Ho);
         const int b = static_cast<int>(p / (static_cast<long>(g.Wo) * g.Ho));
         int iy, ix;
-        if (cx < g.Ci && tap_src(g, oy, ox, ty, tx, &iy, &ix))
-          vx = __bfloat162float(x[((static_cast<long>(b) * g.Hi + iy) * g.Wi + ix) * g.Ci + cx]);
+        if (tap_src(g, oy, ox, ty, tx, &iy, &ix)) src = ((static_cast<long>(b) * g.Hi + iy) * g.Wi + ix) * g.Ci;
       }
-      sdz[pl][c] = vz;
-      sx[pl][c] = vx;
+      ssrc[threadIdx.x] = src;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int pl = 0; pl < 32; ++pl) acc = fmaf(sdz[pl][co_l], sx[pl][ci_l], acc);
+    for (int e = threadIdx.x; e < 32 * TCO; e += 256) {
+      const int pl = e / TCO, c = e % TCO;
+      const long p = pb + pl;
+      const int cz = cot * TCO + c;
+      sdz[pl][c] = (p < p1 && cz < g.Co) ? dz[p * g.Co + cz] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * TCI; e += 256) {
+      const int pl = e / TCI, c = e % TCI;
+      const int cx = cit * TCI + c;
+      const long src = ssrc[pl];
+      sx[pl][c] = (src >= 0 && cx < g.Ci) ? __bfloat162float(x[src + cx]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int pl = 0; pl < 32; ++pl) {
+      float dv[RO], xv[RI];
+#pragma unroll
+      for (int a = 0; a < RO; ++a) dv[a] = sdz[pl][to + 16 * a];
+#pragma unroll
+      for (int b = 0; b < RI; ++b) xv[b] = sx[pl][ti + 16 * b];
+#pragma unroll
+      for (int a = 0; a < RO; ++a)
+#pragma unroll
+        for (int b = 0; b < RI; ++b) acc[a][b] = fmaf(dv[a], xv[b], acc[a][b]);
+    }
     __syncthreads();
   }
-  if (co < g.Co && ci < g.Ci)
-    part[((static_cast<long>(chunk) * g.taps + tap) * g.Co + co) * g.Ci + ci] = acc;
+#pragma unroll
+  for (int a = 0; a < RO; ++a)
+#pragma unroll
+    for (int b = 0; b < RI; ++b) {
+      const int co = cot * TCO + to + 16 * a, ci = cit * TCI + ti + 16 * b;
+      if (co < g.Co && ci < g.Ci)
+        part[((static_cast<long>(chunk) * g.taps + tap) * g.Co + co) * g.Ci + ci] = acc[a][b];
+    }
+}
+
+template <int TCO, int TCI>
+void launch_wgrad(const ConvGeo& g, const bf16* x, const float* dz, float* part, int nch, cudaStream_t st) {
+  const int tiles = g.taps * ((g.Co + TCO - 1) / TCO) * ((g.Ci + TCI - 1) / TCI);
+  k_conv_wgrad<TCO, TCI><<<dim3(tiles, nch), 256, 0, st>>>(g, x, dz, part);
 }
 
 // sum the partials over chunks, add into the master-layout gradient
@@ -296,24 +388,28 @@ __global__ void k_dw_dgrad(const float* __restrict__ dz, int B, int H, int W, in
   }
 }
 
-// partials [chunk][C][9]
+// partials [chunk][C][9]: thread per channel (coalesced), the 9 taps in registers
+constexpr int DW_PIX = 256;
 __global__ void k_dw_wgrad(const bf16* __restrict__ x, const float* __restrict__ dz, int B, int H, int W, int C,
                            float* __restrict__ part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
   const long P = static_cast<long>(B) * H * W;
-  const long p0 = static_cast<long>(blockIdx.y) * WG_PIX, p1 = min(p0 + WG_PIX, P);
-  for (int o = threadIdx.x + blockIdx.x * blockDim.x; o < C * 9; o += blockDim.x * gridDim.x) {
-    const int c = o / 9, tap = o % 9;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    float acc = 0.f;
-    for (long p = p0; p < p1; ++p) {
-      const int xx = static_cast<int>(p % W), yy = static_cast<int>((p / W) % H);
-      const int b = static_cast<int>(p / (static_cast<long>(W) * H));
-      const int sy = yy + dy, sx = xx + dx;
+  const long p0 = static_cast<long>(blockIdx.y) * DW_PIX, p1 = min(p0 + DW_PIX, P);
+  float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long p = p0; p < p1; ++p) {
+    const int xx = static_cast<int>(p % W), yy = static_cast<int>((p / W) % H);
+    const int b = static_cast<int>(p / (static_cast<long>(W) * H));
+    const float d = dz[p * C + c];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
       if (sy < 0 || sy >= H || sx < 0 || sx >= W) continue;
-      acc = fmaf(dz[p * C + c], __bfloat162float(x[((static_cast<long>(b) * H + sy) * W + sx) * C + c]), acc);
+      acc[tap] = fmaf(d, __bfloat162float(x[((static_cast<long>(b) * H + sy) * W + sx) * C + c]), acc[tap]);
     }
-    part[static_cast<long>(blockIdx.y) * C * 9 + o] = acc;
   }
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) part[(static_cast<long>(blockIdx.y) * C + c) * 9 + tap] = acc[tap];
 }
 
 __global__ void k_sum_chunks_add(const float* __restrict__ part, int nchunk, long n, float* __restrict__ out) {
@@ -528,13 +624,15 @@ __global__ void k_greens_bwd(const float* __restrict__ Kpar, int nk, int m, floa
 
 // ---- projection + P backward ----------------------------------------------------------
 // g_p = s * P^T g_e = s * 4 R(g_e) at I/2; du[c] = sum_o w[o][c] g_p[o]; dW, db partials
-__global__ void k_proj_bwd(const float2* __restrict__ ge, const bf16* __restrict__ u, int B, int Nc, int C,
-                           const float* __restrict__ w, const float* __restrict__ s, float* __restrict__ du,
-                           float* __restrict__ part /*[nblk][2*C + 2]*/) {
+__global__ void __launch_bounds__(256) k_proj_bwd(const float2* __restrict__ ge, const bf16* __restrict__ u, int B,
+                                                  int Nc, int C, const float* __restrict__ w,
+                                                  const float* __restrict__ s, float* __restrict__ du,
+                                                  float* __restrict__ part /*[nblk][2*C + 2]*/) {
   const int N = 2 * Nc;
-  extern __shared__ float ps[];  // [2C + 2]
-  for (int i = threadIdx.x; i < 2 * C + 2; i += blockDim.x) ps[i] = 0.f;
-  __syncthreads();
+  constexpr int MAXC = 16;
+  float pw[2 * MAXC + 2];
+#pragma unroll
+  for (int i = 0; i < 2 * MAXC + 2; ++i) pw[i] = 0.f;
   const long total = static_cast<long>(B) * Nc * Nc;
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
@@ -546,23 +644,39 @@ __global__ void k_proj_bwd(const float2* __restrict__ ge, const bf16* __restrict
         const int y = 2 * J + a, x = 2 * K + c;
         if (y < 0 || y >= N || x < 0 || x >= N) continue;
         const float wt = (a == 0 ? 2.f : 1.f) * (c == 0 ? 2.f : 1.f) * 0.25f;
-        const float2 g = ge[(static_cast<long>(b) * N + y) * N + x];
-        acc.x += wt * g.x;
-        acc.y += wt * g.y;
+        const float2 gv = ge[(static_cast<long>(b) * N + y) * N + x];
+        acc.x += wt * gv.x;
+        acc.y += wt * gv.y;
       }
     acc = cscale(acc, s[b]);
     const bf16* up = u + i * C;
-    for (int ch = 0; ch < C; ++ch) {
+#pragma unroll
+    for (int ch = 0; ch < MAXC; ++ch) {
+      if (ch >= C) break;
       du[i * C + ch] += w[ch] * acc.x + w[C + ch] * acc.y;
       const float v = __bfloat162float(up[ch]);
-      atomicAdd(&ps[ch], acc.x * v);
-      atomicAdd(&ps[C + ch], acc.y * v);
+      pw[ch] = fmaf(acc.x, v, pw[ch]);
+      pw[MAXC + ch] = fmaf(acc.y, v, pw[MAXC + ch]);
     }
-    atomicAdd(&ps[2 * C], acc.x);
-    atomicAdd(&ps[2 * C + 1], acc.y);
+    pw[2 * MAXC] += acc.x;
+    pw[2 * MAXC + 1] += acc.y;
+  }
+  __shared__ float red[8][2 * MAXC + 2];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 2 * MAXC + 2; ++i) {
+    const float v = warp_sum(pw[i]);
+    if (lane == 0) red[wp][i] = v;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * C + 2; i += blockDim.x) part[static_cast<long>(blockIdx.x) * (2 * C + 2) + i] = ps[i];
+  if (threadIdx.x < 2 * C + 2) {
+    // output order: w0[0..C), w1[0..C), b0, b1
+    const int t = threadIdx.x;
+    const int src = t < C ? t : (t < 2 * C ? MAXC + (t - C) : 2 * MAXC + (t - 2 * C));
+    float v = 0.f;
+    for (int q = 0; q < (blockDim.x >> 5); ++q) v += red[q][src];
+    part[static_cast<long>(blockIdx.x) * (2 * C + 2) + t] = v;
+  }
 }
 
 // out[i] += sum_k part[k * stride + off + i], i < n
@@ -649,7 +763,8 @@ struct TrainState {
   bool overflow;
 };
 
-static const int kMaxChunks = 512;
+static const int kMaxChunks = 2048;   // BN / projection reduction blocks
+static const int kMaxWChunks = 512;   // weight-gradient pixel chunks
 
 static void carve_train(const helm_cnn* c, int I, int B, Carve& cv, TrainState* T, bool with_backward) {
   build_encoder_plan(c, I, &T->enc, T->enc_out, &T->kf);
@@ -701,7 +816,7 @@ static void carve_train(const helm_cnn* c, int I, int B, Carve& cv, TrainState* 
     T->sgrad[T->x0] = nullptr;
     T->dz_elems = maxel;
     T->dz = cv.take<float>(maxel);
-    T->wpart_elems = static_cast<size_t>(kMaxChunks) * 9 * 64 * 64;
+    T->wpart_elems = static_cast<size_t>(kMaxWChunks) * 9 * 64 * 64;
     T->wpart = cv.take<float>(T->wpart_elems);
     T->bnpart = T->part;
     T->S = cv.take<float>(2 * 384);
@@ -760,12 +875,13 @@ static int run_layers_train(helm_cnn* c, const Plan& pl, const std::vector<void*
     // BN statistics and the epilogue
     const BnInfo& bn = c->bns[L.bn];
     const long P = static_cast<long>(out.B) * out.H * out.W;
-    const int nblk = div_up(P, BN_CHUNK);
+    const long chunk = bn_chunk(P);
+    const int nblk = div_up(P, chunk);
     if (nblk > kMaxChunks) {
       set_error("cnn training: activation too large for the BN reduction");
       return HELM_ESHAPE;
     }
-    HELM_LAUNCH("k_chan_sums", st, k_chan_sums<<<nblk, 256, 2 * bn.C * sizeof(float), st>>>(raw[li], P, bn.C, part));
+    HELM_LAUNCH("k_chan_sums", st, k_chan_sums<<<nblk, chan_block(bn.C), chan_smem(bn.C), st>>>(raw[li], P, bn.C, chunk, part));
     HELM_LAUNCH("k_bn_finalize", st,
                 k_bn_finalize<<<div_up(bn.C, 128), 128, 0, st>>>(part, nblk, bn.C, P, mean[li], istd[li],
                                                                  c->running + bn.roff, c->running + bn.roff + bn.C));
@@ -855,11 +971,12 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
       HELM_LAUNCH("k_add_grad", st, k_add_grad<<<gridn(n_t), 256, 0, st>>>(dY, n_out, n_t, grad[L.add2]));
     }
     // BN + activation
-    const int nblk = div_up(P, BN_CHUNK);
+    const long chunk = bn_chunk(P);
+    const int nblk = div_up(P, chunk);
     HELM_LAUNCH("k_bn_bwd_sums", st,
-                k_bn_bwd_sums<<<nblk, 256, 2 * bn.C * sizeof(float), st>>>(dY, raw[li], P, bn.C, mean[li], istd[li],
+                k_bn_bwd_sums<<<nblk, chan_block(bn.C), chan_smem(bn.C), st>>>(dY, raw[li], P, bn.C, mean[li], istd[li],
                                                                            PP(c, bn.pg), PP(c, bn.pb), L.act,
-                                                                           T.bnpart));
+                                                                           chunk, T.bnpart));
     HELM_LAUNCH("k_bn_bwd_final", st,
                 k_bn_bwd_final<<<div_up(bn.C, 128), 128, 0, st>>>(T.bnpart, nblk, bn.C, T.S,
                                                                   gparams + c->params[bn.pg].offset,
@@ -873,9 +990,13 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
       if (grad[L.in])
         HELM_LAUNCH("k_dw_dgrad", st,
                     k_dw_dgrad<<<gridn(n_out), 256, 0, st>>>(T.dz, in.B, in.H, in.W, in.C, PP(c, L.wparam), grad[L.in]));
-      const int nch = div_up(P, WG_PIX);
+      const int nch = div_up(P, DW_PIX);
+      if (static_cast<size_t>(nch) * in.C * 9 > T.wpart_elems) {
+        set_error("cnn training: depthwise weight-gradient partials exceed the workspace");
+        return HELM_ESHAPE;
+      }
       HELM_LAUNCH("k_dw_wgrad", st,
-                  k_dw_wgrad<<<dim3(div_up(in.C * 9, 256), nch), 256, 0, st>>>(static_cast<const bf16*>(ptr[L.in]),
+                  k_dw_wgrad<<<dim3(div_up(in.C, 64), nch), 64, 0, st>>>(static_cast<const bf16*>(ptr[L.in]),
                                                                               T.dz, in.B, in.H, in.W, in.C, T.wpart));
       HELM_LAUNCH("k_sum_chunks_add", st,
                   k_sum_chunks_add<<<gridn(in.C * 9), 256, 0, st>>>(T.wpart, nch, in.C * 9,
@@ -895,17 +1016,30 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
     g.mode = L.mode == HELM_CONV_T1 ? HELM_CONV_S1 : L.mode;
     g.transposed = (L.mode == HELM_CONV_T1 || L.mode == HELM_CONV_T2) ? 1 : 0;
     if (grad[L.in]) {
-      const long nin = static_cast<long>(in.B) * in.H * in.W * in.C;
-      HELM_LAUNCH("k_conv_dgrad", st, k_conv_dgrad<<<gridn(nin), 256, 0, st>>>(g, T.dz, PP(c, L.wparam), grad[L.in]));
+      const long nw = static_cast<long>(g.taps) * g.Co * g.Ci;
+      HELM_LAUNCH("k_pack_dgrad_w", st, k_pack_dgrad_w<<<gridn(nw), 256, 0, st>>>(g, PP(c, L.wparam), T.wpart));
+      const long nin = static_cast<long>(in.B) * in.H * in.W * (in.C / 8);
+      HELM_LAUNCH("k_conv_dgrad", st, k_conv_dgrad<<<gridn(nin), 256, 0, st>>>(g, T.dz, T.wpart, grad[L.in]));
     }
     const int nch = div_up(P, WG_PIX);
     if (static_cast<size_t>(nch) * g.taps * g.Co * g.Ci > T.wpart_elems) {
       set_error("cnn training: weight-gradient partials exceed the workspace");
       return HELM_ESHAPE;
     }
-    const int tiles = g.taps * div_up(g.Co, 16) * div_up(g.Ci, 16);
-    HELM_LAUNCH("k_conv_wgrad", st,
-                k_conv_wgrad<<<dim3(tiles, nch), 256, 0, st>>>(g, static_cast<const bf16*>(ptr[L.in]), T.dz, T.wpart));
+    {
+      const bf16* xin = static_cast<const bf16*>(ptr[L.in]);
+      const int tco = g.Co >= 64 ? 64 : (g.Co >= 32 ? 32 : 16);
+      const int tci = g.Ci >= 64 ? 64 : (g.Ci >= 32 ? 32 : 16);
+      if (tco == 64 && tci == 64) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<64, 64>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tco == 64 && tci == 32) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<64, 32>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tco == 32 && tci == 64) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<32, 64>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tco == 32 && tci == 32) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<32, 32>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tco == 64) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<64, 16>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tci == 64) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<16, 64>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tco == 32) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<32, 16>(g, xin, T.dz, T.wpart, nch, st));
+      else if (tci == 32) HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<16, 32>(g, xin, T.dz, T.wpart, nch, st));
+      else HELM_LAUNCH("k_conv_wgrad", st, launch_wgrad<16, 16>(g, xin, T.dz, T.wpart, nch, st));
+    }
     HELM_LAUNCH("k_wgrad_reduce", st,
                 k_wgrad_reduce<<<gridn(static_cast<long>(g.taps) * g.Co * g.Ci), 256, 0, st>>>(
                     g, T.wpart, nch, gparams + c->params[L.wparam].offset));
@@ -941,7 +1075,7 @@ int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gp
     const long tot = static_cast<long>(B) * Nc * Nc;
     const int nblk = std::min<int>(kMaxChunks, gridn(tot));
     HELM_LAUNCH("k_proj_bwd", st,
-                k_proj_bwd<<<nblk, 256, (2 * C + 2) * sizeof(float), st>>>(ge, static_cast<const bf16*>(T.sptr[T.u3]),
+                k_proj_bwd<<<nblk, 256, 0, st>>>(ge, static_cast<const bf16*>(T.sptr[T.u3]),
                                                                          B, Nc, C, c->params_dev + pw.offset, T.s,
                                                                          T.sgrad[T.u3], T.ppart));
     HELM_LAUNCH("k_strided_reduce", st,

@@ -88,7 +88,7 @@ def test_bn_eval_folding_equivalence():
 
 
 def test_eval_forward_is_scale_equivariant_and_zero_safe():
-    """Reading A10: e = ||r|| Net(r/||r||), so Net(c r) = |c| ... for c > 0."""
+    """Reading A10: e = s Net(r/s) with s = RMS(r), so e(c r) = c e(r) for c > 0."""
     net, P, kf, r, _ = _setup(B=2)
     e1, _ = net.forward(r, kf, train=False)
     e2, _ = net.forward(3.0 * r, kf, train=False)
@@ -111,7 +111,8 @@ def test_training_pairs_satisfy_r_equals_A_e():
     rel = [np.linalg.norm(r[i]) / np.linalg.norm(prob.A(x[i])) for i in range(3)]
     assert rel[2] < rel[0]
     en, rn = tr.normalise_pairs(e, r)
-    assert np.allclose([np.linalg.norm(v) for v in rn], 1.0)
+    assert np.allclose([np.sqrt(np.mean(np.abs(v) ** 2)) for v in rn], 1.0)
+    assert np.allclose(rn[1], r[1] / np.sqrt(np.mean(np.abs(r[1]) ** 2)))
 
 
 def test_mse_loss_gradient_and_adam_first_step():
