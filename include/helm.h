@@ -241,10 +241,19 @@ int helm_cnn_set_problem(helm_cnn* c, const helm_problem* p, void* ws, size_t ws
 int helm_cnn_apply(const helm_problem* p, helm_cnn* c, const void* r, void* e, int batch, int train, void* ws,
                    size_t ws_bytes, void* stream);
 
-/* Bytes of the training workspace for helm_cnn_apply(train = 1) followed by
+/* Bytes of the training workspace for a training forward over `nprob` slowness models
+ * (helm_cnn_train_forward, or helm_cnn_apply(train = 1) with nprob = 1) followed by
  * helm_cnn_precond_backward at this batch size (activations, raw BN inputs, statistics,
  * gradients of every activation, reduction partials). */
-int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int batch, size_t* bytes);
+int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int batch, int nprob, size_t* bytes);
+
+/* Training-mode forward over a batch whose samples come from several slowness models
+ * (Section 4.3, Eq. 16: each pair carries its own kappa): sample b belongs to
+ * probs[b / (batch / nprob)] (batch divisible by nprob, equal grids).  The encoder runs
+ * on the nprob models, batch-statistics BN, activations saved in ws for
+ * helm_cnn_precond_backward, running statistics updated. */
+int helm_cnn_train_forward(const helm_problem* const* probs, int nprob, helm_cnn* c, const void* r, void* e,
+                           int batch, void* ws, size_t ws_bytes, void* stream);
 
 /* Backward of the last training-mode helm_cnn_apply that used the same workspace:
  * grad_e (complex64 [batch][N][N], dLoss/dRe e + i dLoss/dIm e) -> grad_params (FP32,

@@ -299,13 +299,16 @@ def softplus(tp: Tape, x: Var) -> Var:
 
 
 def add(tp: Tape, x: Var, y: Var) -> Var:
-    """x + y with y broadcast over the batch if it has batch size 1."""
-    out = Var(x.a + y.a)
+    """x + y; if y has fewer batch entries (G dividing B), entry g is added to the g-th
+    group of B/G consecutive samples (each slowness model's encoding feeds the samples
+    drawn for it; G = 1 is a plain broadcast)."""
+    B, G = x.a.shape[0], y.a.shape[0]
+    rep = B // G
+    out = Var(x.a + np.repeat(y.a, rep, axis=0))
 
     def bwd():
         x.acc(out.g)
-        gy = out.g if y.a.shape[0] == out.g.shape[0] else out.g.sum(axis=0, keepdims=True)
-        y.acc(gy)
+        y.acc(out.g.reshape((G, rep) + out.g.shape[1:]).sum(axis=1))
     tp.push(bwd)
     return out
 

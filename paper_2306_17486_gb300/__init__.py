@@ -316,29 +316,37 @@ class Cnn:
         return z
 
     # ---- training ---------------------------------------------------------------
-    def train_workspace(self, p: Problem, batch: int) -> torch.Tensor:
+    def train_workspace(self, p: Problem, batch: int, nprob: int = 1) -> torch.Tensor:
         n = C.c_size_t()
-        check(lib().helm_cnn_train_workspace_size(p.handle, self.handle, batch, C.byref(n)), "train_workspace_size")
+        check(lib().helm_cnn_train_workspace_size(p.handle, self.handle, batch, nprob, C.byref(n)),
+              "train_workspace_size")
         ws = getattr(self, "_tws", None)
         if ws is None or ws.numel() < n.value:
             self._tws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
         return self._tws
 
-    def forward_train(self, p: Problem, r: torch.Tensor) -> torch.Tensor:
-        """Training-mode forward (batch-statistics BN; saves activations for backward)."""
+    def forward_train(self, p, r: torch.Tensor) -> torch.Tensor:
+        """Training-mode forward (batch-statistics BN; saves activations for backward).
+        `p` is one Problem or a list of Problems: sample b then belongs to
+        p[b // (B // len(p))]."""
         _need(r, torch.complex64, "r")
         B = r.shape[0]
-        ws = self.train_workspace(p, B)
+        probs = list(p) if isinstance(p, (list, tuple)) else [p]
+        ws = self.train_workspace(probs[0], B, len(probs))
         e = torch.empty_like(r)
-        check(lib().helm_cnn_apply(p.handle, self.handle, _ptr(r), _ptr(e), B, 1, _ptr(ws), ws.numel(), _stream()),
-              "helm_cnn_apply(train)")
+        arr = (C.c_void_p * len(probs))(*[q.handle.value for q in probs])
+        check(lib().helm_cnn_train_forward(arr, len(probs), self.handle, _ptr(r), _ptr(e), B, _ptr(ws), ws.numel(),
+                                           _stream()), "helm_cnn_train_forward")
+        self._train_nprob = len(probs)
+        self._train_p0 = probs[0]
         return e
 
-    def backward(self, p: Problem, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None) -> torch.Tensor:
+    def backward(self, p, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None) -> torch.Tensor:
         _need(grad_e, torch.complex64, "grad_e")
         B = grad_e.shape[0]
         g = torch.empty_like(self.params) if grad_params is None else grad_params
-        ws = self.train_workspace(p, B)
+        p = p[0] if isinstance(p, (list, tuple)) else p
+        ws = self.train_workspace(p, B, getattr(self, "_train_nprob", 1))
         check(lib().helm_cnn_precond_backward(p.handle, self.handle, _ptr(grad_e), _ptr(g), B, _ptr(ws), ws.numel(),
                                               _stream()), "helm_cnn_precond_backward")
         return g

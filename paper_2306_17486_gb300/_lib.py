@@ -74,7 +74,8 @@ PROTOS = {
     "helm_cnn_apply": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp]),
     "helm_cnn_precond_apply": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
     "helm_cnn_precond_backward": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
-    "helm_cnn_train_workspace_size": (i32, [vp, vp, i32, C.POINTER(sz)]),
+    "helm_cnn_train_workspace_size": (i32, [vp, vp, i32, i32, C.POINTER(sz)]),
+    "helm_cnn_train_forward": (i32, [C.POINTER(vp), i32, vp, vp, vp, i32, vp, sz, vp]),
     "helm_mse_loss": (i32, [vp, vp, C.c_long, i32, vp, vp, vp, vp]),
     "helm_adam_step": (i32, [vp, vp, vp, vp, C.c_long, f64, f64, f64, f64, i32, vp]),
 }

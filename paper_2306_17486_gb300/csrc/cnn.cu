@@ -127,19 +127,19 @@ static Layer conv_layer(const helm_cnn* c, const std::string& w, const std::stri
   return L;
 }
 
-void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf) {
+void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, int Bk) {
   *pl = Plan();
   pl->I = I;
-  pl->B = 1;
+  pl->B = Bk;
   const int C[3] = {c->desc.c0, 2 * c->desc.c0, 4 * c->desc.c0};
-  *kf = pl->add_tensor(1, I, I, 2);
+  *kf = pl->add_tensor(Bk, I, I, 2);
   int x = *kf, H = I;
   for (int k = 0; k < 3; ++k) {
     H /= 2;
     const std::string p = "e.dm" + std::to_string(k + 1);
-    const int a = pl->add_tensor(1, H, H, C[k]);
-    const int b = pl->add_tensor(1, H, H, C[k]);
-    const int o = pl->add_tensor(1, H, H, C[k]);
+    const int a = pl->add_tensor(Bk, H, H, C[k]);
+    const int b = pl->add_tensor(Bk, H, H, C[k]);
+    const int o = pl->add_tensor(Bk, H, H, C[k]);
     pl->layers.push_back(conv_layer(c, p + ".conv0.w", p + ".bn0", HELM_CONV_S2, x, a, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv1.w", p + ".bn1", HELM_CONV_S1, a, b, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv2.w", p + ".bn2", HELM_CONV_S1, b, o, -1, -1));
@@ -148,7 +148,8 @@ void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf) 
   }
 }
 
-void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3]) {
+void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
+                       int Bk) {
   *pl = Plan();
   pl->I = I;
   pl->B = B;
@@ -160,7 +161,7 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
   // encodings live in the encoder's arena: placeholders, resolved at run time
   for (int k = 0; k < 3; ++k) {
     const int h = I >> (k + 1);
-    TensorDesc d{1, h, h, C[k], ~size_t(0)};
+    TensorDesc d{Bk, h, h, C[k], ~size_t(0)};
     pl->t.push_back(d);
     enc_ids[k] = static_cast<int>(pl->t.size()) - 1;
   }
@@ -337,7 +338,7 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
       cl.act = L.act;
       cl.add1 = L.add1 >= 0 ? static_cast<const __nv_bfloat16*>(ptr[L.add1]) : nullptr;
       cl.add2 = L.add2 >= 0 ? static_cast<const __nv_bfloat16*>(ptr[L.add2]) : nullptr;
-      cl.add2_bcast = (L.add2 >= 0 && pl.t[L.add2].B == 1 && out.B > 1) ? 1 : 0;
+      cl.add2_div = L.add2 >= 0 ? out.B / pl.t[L.add2].B : 1;
       cl.y = static_cast<__nv_bfloat16*>(ptr[L.out]);
       rc = conv_tc(cl, st);
     } else if (L.kind == L_DW) {
@@ -357,7 +358,7 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
 size_t cnn_forward_bytes(const helm_cnn* c, int I, int B) {
   Plan pl;
   int x0, u3, e[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, e);
+  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, e, 1);
   return pl.arena + static_cast<size_t>(B) * 256 * sizeof(double) + 2 * 256 * B * sizeof(float) + 4096;
 }
 
@@ -371,7 +372,7 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
   const int I = p->nx;
   Plan pl;
   int x0, u3, enc[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, enc);
+  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, enc, 1);
   int rc = cnn_derive(c, pl.m, st);
   if (rc) return rc;
   char* arena = cv.take<char>(pl.arena);
@@ -403,7 +404,7 @@ int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
   int rc = cnn_derive(c, 0, st);
   if (rc) return rc;
   if (c->enc_I != I || !c->enc_arena) {
-    build_encoder_plan(c, I, &c->enc_plan, c->enc_out, &c->kf);
+    build_encoder_plan(c, I, &c->enc_plan, c->enc_out, &c->kf, 1);
     cudaFree(c->enc_arena);
     c->enc_arena = nullptr;
     if (cudaMalloc(&c->enc_arena, c->enc_plan.arena) != cudaSuccess) {
@@ -592,7 +593,7 @@ int helm_cnn_apply(const helm_problem* p, helm_cnn* c, const void* r, void* e, i
     return HELM_EINVAL;
   }
   helm::Carve cv(ws, ws_bytes);
-  if (train) return helm::cnn_forward_train(c, p, static_cast<const float2*>(r), static_cast<float2*>(e), batch, cv,
+  if (train) return helm::cnn_forward_train(c, &p, 1, static_cast<const float2*>(r), static_cast<float2*>(e), batch, cv,
                                             static_cast<cudaStream_t>(stream));
   return helm::cnn_forward_infer(c, p, static_cast<const float2*>(r), static_cast<float2*>(e), batch, cv,
                                  static_cast<cudaStream_t>(stream));

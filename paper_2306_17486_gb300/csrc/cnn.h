@@ -20,7 +20,7 @@ struct ConvLaunch {
   int act = 0;
   const __nv_bfloat16* add1 = nullptr;
   const __nv_bfloat16* add2 = nullptr;
-  int add2_bcast = 0;
+  int add2_div = 1;   // consecutive samples sharing one add2 entry
   __nv_bfloat16* y = nullptr;
   float* yraw = nullptr;
 };

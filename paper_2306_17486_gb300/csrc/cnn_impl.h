@@ -83,22 +83,24 @@ struct helm_cnn {
   helm::Plan enc_plan;
   int enc_out[3] = {-1, -1, -1};
   int kf = -1;
+  int train_nprob = 0;  // slowness models of the last training forward
 };
 
 namespace helm {
 
 // parameter and BN lookup
 inline int P(const helm_cnn* c, const std::string& n) { return c->pidx.at(n); }
-void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf);
-void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3]);
+void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, int Bk);
+void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
+                       int Bk);
 int cnn_derive(helm_cnn* c, int m, cudaStream_t st);  // pack weights, fold BN, build G_hat(m)
 int skip_for(const helm_cnn* c, int I);
 size_t packed_elems(const helm_cnn* c, const ParamInfo& pi);
 size_t wpk_offset(const helm_cnn* c, int param);
-size_t cnn_train_bytes(const helm_cnn* c, int I, int B);
+size_t cnn_train_bytes(const helm_cnn* c, int I, int B, int nprob);
 int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float2* e, int B, Carve& cv,
                       cudaStream_t st);
-int cnn_forward_train(helm_cnn* c, const helm_problem* p, const float2* r, float2* e, int B, Carve& cv,
-                      cudaStream_t st);
+int cnn_forward_train(helm_cnn* c, const helm_problem* const* probs, int nprob, const float2* r, float2* e, int B,
+                      Carve& cv, cudaStream_t st);
 
 }  // namespace helm

@@ -81,18 +81,22 @@ __global__ void k_bn_finalize(const double* __restrict__ part, int nblk, int C, 
   }
 }
 
-// y = act(g (z - mu) istd + b) + add1 + add2(bcast) -> bf16
+// y = act(g (z - mu) istd + b) + add1 + add2 -> bf16; add2 has one entry per group of
+// `div` consecutive samples (sample_elems elements per sample)
 __global__ void k_bn_apply(const float* __restrict__ z, long P, int C, const float* __restrict__ mean,
                            const float* __restrict__ istd, const float* __restrict__ g, const float* __restrict__ b,
-                           int act, const bf16* __restrict__ add1, const bf16* __restrict__ add2, long bcast_pix,
-                           bf16* __restrict__ y) {
+                           int act, const bf16* __restrict__ add1, const bf16* __restrict__ add2, long sample_elems,
+                           int div, bf16* __restrict__ y) {
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < P * C;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
     const int c = static_cast<int>(i % C);
     float v = g[c] * (z[i] - mean[c]) * istd[c] + b[c];
     if (act) v = spf(v);
     if (add1) v += __bfloat162float(add1[i]);
-    if (add2) v += __bfloat162float(add2[bcast_pix ? (i % (bcast_pix * C)) : i]);
+    if (add2) {
+      const long smp = i / sample_elems;
+      v += __bfloat162float(add2[(smp / div) * sample_elems + (i - smp * sample_elems)]);
+    }
     y[i] = __float2bfloat16_rn(v);
   }
 }
@@ -161,12 +165,14 @@ __global__ void k_bn_bwd_apply(const float* __restrict__ dY, const float* __rest
   }
 }
 
-// dT += dY (same shape), or the batch sum of dY when dT has batch 1
-__global__ void k_add_grad(const float* __restrict__ dY, long n_out, long n_t, float* __restrict__ dT) {
+// dT += dY summed over each group of `div` consecutive samples (div = 1: same shape)
+__global__ void k_add_grad(const float* __restrict__ dY, long n_t, long sample_elems, int div,
+                           float* __restrict__ dT) {
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n_t;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const long grp = i / sample_elems, off = i - grp * sample_elems;
     float s = 0.f;
-    for (long j = i; j < n_out; j += n_t) s += dY[j];
+    for (int q = 0; q < div; ++q) s += dY[(grp * div + q) * sample_elems + off];
     dT[i] += s;
   }
 }
@@ -766,9 +772,9 @@ struct TrainState {
 static const int kMaxChunks = 2048;   // BN / projection reduction blocks
 static const int kMaxWChunks = 512;   // weight-gradient pixel chunks
 
-static void carve_train(const helm_cnn* c, int I, int B, Carve& cv, TrainState* T, bool with_backward) {
-  build_encoder_plan(c, I, &T->enc, T->enc_out, &T->kf);
-  build_solver_plan(c, I, B, skip_for(c, I), &T->sol, &T->x0, &T->u3, T->enc_ids);
+static void carve_train(const helm_cnn* c, int I, int B, int nprob, Carve& cv, TrainState* T, bool with_backward) {
+  build_encoder_plan(c, I, &T->enc, T->enc_out, &T->kf, nprob);
+  build_solver_plan(c, I, B, skip_for(c, I), &T->sol, &T->x0, &T->u3, T->enc_ids, nprob);
   char* ea = cv.take<char>(T->enc.arena);
   char* sa = cv.take<char>(T->sol.arena);
   T->eptr.resize(T->enc.t.size());
@@ -830,10 +836,10 @@ static void carve_train(const helm_cnn* c, int I, int B, Carve& cv, TrainState* 
   T->overflow = cv.overflow;
 }
 
-size_t cnn_train_bytes(const helm_cnn* c, int I, int B) {
+size_t cnn_train_bytes(const helm_cnn* c, int I, int B, int nprob) {
   Carve cv(nullptr, ~size_t(0));
   TrainState T;
-  carve_train(c, I, B, cv, &T, true);
+  carve_train(c, I, B, nprob, cv, &T, true);
   return cv.off + 4096;
 }
 
@@ -885,34 +891,47 @@ static int run_layers_train(helm_cnn* c, const Plan& pl, const std::vector<void*
     HELM_LAUNCH("k_bn_finalize", st,
                 k_bn_finalize<<<div_up(bn.C, 128), 128, 0, st>>>(part, nblk, bn.C, P, mean[li], istd[li],
                                                                  c->running + bn.roff, c->running + bn.roff + bn.C));
-    const bool bc = L.add2 >= 0 && pl.t[L.add2].B == 1 && out.B > 1;
+    const int div2 = L.add2 >= 0 ? out.B / pl.t[L.add2].B : 1;
     HELM_LAUNCH("k_bn_apply", st,
                 k_bn_apply<<<gridn(P * bn.C), 256, 0, st>>>(
                     raw[li], P, bn.C, mean[li], istd[li], PP(c, bn.pg), PP(c, bn.pb), L.act,
                     L.add1 >= 0 ? static_cast<const bf16*>(ptr[L.add1]) : nullptr,
                     L.add2 >= 0 ? static_cast<const bf16*>(ptr[L.add2]) : nullptr,
-                    bc ? static_cast<long>(out.H) * out.W : 0, static_cast<bf16*>(ptr[L.out])));
+                    static_cast<long>(out.H) * out.W * bn.C, div2, static_cast<bf16*>(ptr[L.out])));
     HELM_CHECK_LAUNCH("bn train");
   }
   return HELM_OK;
 }
 
-int cnn_forward_train(helm_cnn* c, const helm_problem* p, const float2* r, float2* e, int B, Carve& cv,
-                      cudaStream_t st) {
+int cnn_forward_train(helm_cnn* c, const helm_problem* const* probs, int nprob, const float2* r, float2* e, int B,
+                      Carve& cv, cudaStream_t st) {
+  const helm_problem* p = probs[0];
   const int I = p->nx;
   if (p->nx != p->ny || I % 16) {
     set_error("cnn: the network needs a square grid divisible by 16");
     return HELM_ESHAPE;
   }
+  if (nprob < 1 || B % nprob) {
+    set_error("cnn training: batch %d not divisible by the %d slowness models", B, nprob);
+    return HELM_EINVAL;
+  }
+  for (int k = 1; k < nprob; ++k)
+    if (probs[k]->nx != I || probs[k]->ny != I) {
+      set_error("cnn training: all slowness models of a batch need the same grid");
+      return HELM_ESHAPE;
+    }
   TrainState T;
-  carve_train(c, I, B, cv, &T, true);
+  carve_train(c, I, B, nprob, cv, &T, true);
   if (T.overflow) {
     set_error("cnn training: workspace too small (helm_cnn_train_workspace_size)");
     return HELM_EWORKSPACE;
   }
   int rc = cnn_derive(c, T.sol.m, st);
   if (rc) return rc;
-  if ((rc = launch_kfeat(p->kappa, p->gamma, p->npts(0), static_cast<bf16*>(T.eptr[T.kf]), st))) return rc;
+  for (int k = 0; k < nprob; ++k)
+    if ((rc = launch_kfeat(probs[k]->kappa, probs[k]->gamma, p->npts(0),
+                           static_cast<bf16*>(T.eptr[T.kf]) + static_cast<size_t>(k) * p->npts(0) * 2, st)))
+      return rc;
   if ((rc = run_layers_train(c, T.enc, T.eptr, T.eraw, T.emean, T.eistd, T.part, st))) return rc;
   if ((rc = launch_prep(r, I, B, T.part, T.s, T.inv, static_cast<bf16*>(T.sptr[T.x0]), st))) return rc;
   if ((rc = run_layers_train(c, T.sol, T.sptr, T.sraw, T.smean, T.sistd, T.part, st))) return rc;
@@ -923,6 +942,7 @@ int cnn_forward_train(helm_cnn* c, const helm_problem* p, const float2* r, float
   if (rc) return rc;
   c->enc_prob = nullptr;  // the cached evaluation-mode encodings are stale now
   c->dirty = true;        // running statistics moved: refold before the next inference
+  c->train_nprob = nprob;
   return HELM_OK;
 }
 
@@ -963,12 +983,14 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
     const long P = static_cast<long>(out.B) * out.H * out.W;
     const long n_out = P * bn.C;
     // additive skips receive dY unchanged (batch-summed for a broadcast encoding)
+    const long selem = static_cast<long>(out.H) * out.W * bn.C;
     if (L.add1 >= 0 && grad[L.add1])
-      HELM_LAUNCH("k_add_grad", st, k_add_grad<<<gridn(n_out), 256, 0, st>>>(dY, n_out, n_out, grad[L.add1]));
+      HELM_LAUNCH("k_add_grad", st, k_add_grad<<<gridn(n_out), 256, 0, st>>>(dY, n_out, selem, 1, grad[L.add1]));
     if (L.add2 >= 0 && grad[L.add2]) {
       const TensorDesc& a2 = pl.t[L.add2];
       const long n_t = static_cast<long>(a2.B) * a2.H * a2.W * a2.C;
-      HELM_LAUNCH("k_add_grad", st, k_add_grad<<<gridn(n_t), 256, 0, st>>>(dY, n_out, n_t, grad[L.add2]));
+      HELM_LAUNCH("k_add_grad", st,
+                  k_add_grad<<<gridn(n_t), 256, 0, st>>>(dY, n_t, selem, out.B / a2.B, grad[L.add2]));
     }
     // BN + activation
     const long chunk = bn_chunk(P);
@@ -1051,8 +1073,12 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
 int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gparams, int B, Carve& cv,
                  cudaStream_t st) {
   const int I = p->nx;
+  if (c->train_nprob < 1) {
+    set_error("cnn backward: no training forward to differentiate");
+    return HELM_ESTATE;
+  }
   TrainState T;
-  carve_train(c, I, B, cv, &T, true);
+  carve_train(c, I, B, c->train_nprob, cv, &T, true);
   if (T.overflow) {
     set_error("cnn backward: workspace too small");
     return HELM_EWORKSPACE;
@@ -1095,13 +1121,29 @@ int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gp
 
 extern "C" {
 
-int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int batch, size_t* bytes) {
-  if (!p || !c || !bytes || batch <= 0) {
+int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int batch, int nprob, size_t* bytes) {
+  if (!p || !c || !bytes || batch <= 0 || nprob < 1) {
     helm::set_error("helm_cnn_train_workspace_size: invalid argument");
     return HELM_EINVAL;
   }
-  *bytes = helm::cnn_train_bytes(c, p->nx, batch);
+  *bytes = helm::cnn_train_bytes(c, p->nx, batch, nprob);
   return HELM_OK;
+}
+
+int helm_cnn_train_forward(const helm_problem* const* probs, int nprob, helm_cnn* c, const void* r, void* e,
+                           int batch, void* ws, size_t ws_bytes, void* stream) {
+  if (!probs || nprob < 1 || !c || !r || !e || batch <= 0 || !ws) {
+    helm::set_error("helm_cnn_train_forward: invalid argument");
+    return HELM_EINVAL;
+  }
+  for (int k = 0; k < nprob; ++k)
+    if (!probs[k]) {
+      helm::set_error("helm_cnn_train_forward: null problem %d", k);
+      return HELM_EINVAL;
+    }
+  helm::Carve cv(ws, ws_bytes);
+  return helm::cnn_forward_train(c, probs, nprob, static_cast<const float2*>(r), static_cast<float2*>(e), batch, cv,
+                                 static_cast<cudaStream_t>(stream));
 }
 
 int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* grad_e, float* grad_params, int batch,

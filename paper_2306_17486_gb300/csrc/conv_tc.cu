@@ -41,8 +41,8 @@ struct ConvArgs {
   const float* shift;    // [COUT] or null (0)
   int act;               // softplus
   const bf16* add1;      // [B][Ho][Wo][COUT] or null
-  const bf16* add2;      // [B or 1][Ho][Wo][COUT] or null
-  int add2_bcast;
+  const bf16* add2;      // [B / add2_div][Ho][Wo][COUT] or null
+  int add2_div;          // consecutive samples sharing one add2 entry (1: per sample)
   bf16* y;               // bf16 NHWC output or null
   float* yraw;           // fp32 NHWC raw accumulator or null
   int tiles_per_img, ntiles;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
     const int y = q / a.Po, x = q % a.Po;
     const bool valid = ok && y < a.Ho && x < a.Wo;
     const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
-    const long pix2 = a.add2_bcast ? static_cast<long>(y) * a.Wo + x : pix;
+    const long pix2 = (static_cast<long>(b / a.add2_div) * a.Ho + y) * a.Wo + x;
 #pragma unroll 1
     for (int c0 = 0; c0 < COUT; c0 += 16) {
       float v[16];
@@ -330,7 +330,7 @@ int conv_tc(const ConvLaunch& c, cudaStream_t st) {
   a.act = c.act;
   a.add1 = c.add1;
   a.add2 = c.add2;
-  a.add2_bcast = c.add2_bcast;
+  a.add2_div = c.add2_div > 0 ? c.add2_div : 1;
   a.y = c.y;
   a.yraw = c.yraw;
   const int taps = c.taps;
@@ -419,7 +419,7 @@ extern "C" int helm_conv_bf16(const void* x, int batch, int hi, int wi, int cin,
   c.act = act;
   c.add1 = static_cast<const bf16*>(add1);
   c.add2 = static_cast<const bf16*>(add2);
-  c.add2_bcast = add2_bcast;
+  c.add2_div = add2_bcast ? batch : 1;
   c.y = static_cast<bf16*>(y);
   c.yraw = yraw;
   return conv_tc(c, st);

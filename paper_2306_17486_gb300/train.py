@@ -4,8 +4,9 @@ by the plain SL-multigrid FGMRES (Section 4.3, Eq. 16-17; Section 5.3).
 Pairs are normalised by the residual's RMS over the grid (the library's reading of the
 unstated input scale), so inputs are O(1) at every grid size.
 
-Every step: one slowness model from a seeded pool of the step's grid size (absorbing
-layer included, gamma = 0.05 as in Section 4.3), a batch of random smooth-plus-noise
+Every step: `kappas_per_batch` slowness models from a seeded pool of the step's grid size
+(absorbing layer included, gamma = 0.05 as in Section 4.3; Eq. 16: each pair carries
+its own kappa, so BatchNorm statistics average over models), a batch of random smooth-plus-noise
 vectors x (inputs: drawn with a seeded torch generator on the device), per-sample
 iteration counts k ~ U{2..20}, then on the library's kernels:
     (e, r) = Eq. (17) pairs, normalised by ||r||      helm_datagen_pairs
@@ -61,9 +62,10 @@ class Trainer:
 
     def __init__(self, net: Cnn, sizes=((128, 16), (256, 16)), batch: int = 32, lr: float = 1e-3,
                  steps: int = 2000, seed: int = 0, pool: int = 24, levels: int = 3, kappa_ell: float = 8.0,
-                 block: int = 100, device="cuda"):
+                 block: int = 100, kappas_per_batch: int = 4, device="cuda"):
         import synth
         self.net, self.batch, self.steps, self.block = net, batch, steps, block
+        self.G = kappas_per_batch
         self.lr0 = lr
         self.device = torch.device(device)
         self.gen = torch.Generator(device=self.device)
@@ -97,14 +99,21 @@ class Trainer:
     def step(self) -> float:
         i = self.step_i
         si = self.size_index(i)
-        p = self.pools[si][int(self.rng.integers(len(self.pools[si])))]
-        N = p.nx
-        x = smooth_plus_noise(self.batch, N, self.gen, device=self.device)
-        k = torch.randint(2, 21, (self.batch,), generator=self.gen, device=self.device, dtype=torch.int32)
-        e, r = datagen_pairs(p, x, k, max_iters=20, normalise=True)
-        e_pred = self.net.forward_train(p, r)
+        pool = self.pools[si]
+        probs = [pool[int(j)] for j in self.rng.choice(len(pool), size=self.G, replace=False)]
+        N = probs[0].nx
+        per = self.batch // self.G
+        es, rs = [], []
+        for p in probs:   # Eq. (17) pairs, `per` samples for each slowness model
+            x = smooth_plus_noise(per, N, self.gen, device=self.device)
+            k = torch.randint(2, 21, (per,), generator=self.gen, device=self.device, dtype=torch.int32)
+            e1, r1 = datagen_pairs(p, x, k, max_iters=20, normalise=True)
+            es.append(e1)
+            rs.append(r1)
+        e, r = torch.cat(es), torch.cat(rs)
+        e_pred = self.net.forward_train(probs, r)
         loss, g = mse_loss(e_pred, e)
-        grads = self.net.backward(p, g)
+        grads = self.net.backward(probs, g)
         self.opt.lr = self.lr_at(i)
         self.opt.step(grads)
         self.net.set_params()

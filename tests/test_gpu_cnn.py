@@ -208,3 +208,36 @@ def test_datagen_pairs_match_oracle(helm):
         # the pair is consistent: r = A e (to FP32 rounding of the stored pair)
         Ae = op.A(e[i].astype(np.complex128))
         assert np.linalg.norm(Ae - r[i]) <= 1e-4 * np.linalg.norm(Ae) + 8 * rel
+
+
+def test_training_with_several_slowness_models_per_batch(helm):
+    """Eq. (16) batches whose pairs come from different kappa: the encoder runs on each
+    model, sample groups add their model's encodings; forward and gradients vs the
+    oracle with grouped encodings."""
+    I, abl, B, G = 64, 8, 4, 2
+    P, _ = _random_net(31)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn()
+    net.load_dict(Pq)
+    probs, kfs = [], []
+    for j in range(G):
+        kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 40 + j).astype(np.float32).astype(np.float64)
+        oh = ohz.omega_h_for_ppw(kappa.max())
+        probs.append(helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, gamma0=0.05,
+                                  levels=3))
+        op = ohz.Problem(kappa, abl, omega_h=oh, gamma0=0.05)
+        kfs.append(ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64)))
+    kf = np.concatenate(kfs)
+    r = synth.random_complex((B, I, I), 8).astype(np.complex64).astype(np.complex128)
+    et = 0.3 * synth.random_complex((B, I, I), 9).astype(np.complex64).astype(np.complex128)
+    eg = net.forward_train(probs, torch.tensor(r, dtype=torch.complex64, device="cuda"))
+    loss, ge = helm.mse_loss(eg, torch.tensor(et, dtype=torch.complex64, device="cuda"))
+    grads = net.to_dict(net.backward(probs, ge))
+    on = ocnn.Network(Pq, None, c0=16)
+    from oracle.training import mse_loss as omse
+    e_ref, tp = on.forward(r, kf, train=True, record=True)
+    L, g_e = omse(e_ref, et)
+    ref = on.backward(tp, g_e)
+    assert np.linalg.norm(eg.cpu().numpy() - e_ref) <= 4e-2 * np.linalg.norm(e_ref)
+    worst = max(np.linalg.norm(grads[n] - ref[n]) / np.linalg.norm(ref[n]) for n in ref if np.linalg.norm(ref[n]) > 0)
+    assert worst < 0.1, worst
