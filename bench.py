@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms per RHS to 1e-6 rel. residual, CNN+MG vs MG-only preconditioned FGMRES"
 N_INT, ABL, LEVELS = 512, 32, 4
-N_MODELS, N_RHS, RESTART, RTOL, MAXIT = 4, 64, 10, 1e-6, 3000
+N_MODELS, N_RHS, RESTART, RTOL, MAXIT = 4, 64, 10, 1e-6, 2000
 WORKLOAD = "helmholtz-576sq-4kappa-x64rhs-fgmres10"
 
 

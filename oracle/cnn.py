@@ -431,14 +431,14 @@ class Network:
     def forward(self, r: np.ndarray, kfeat: np.ndarray, train: bool = False,
                 skip: bool | None = None, record: bool = False):
         """e = s * Net(r / s), s = RMS of r over the grid, for a batch r [B, I, I] complex
-        (reading A10).
+        (the paper leaves the scale unstated; the RMS is this implementation's choice).
 
         Returns (e, tape, scale); the tape's backward accumulates parameter
         gradients in tape.grads given the complex gradient of the loss w.r.t. e.
         """
         B, I, _ = r.shape
         skip = skip_last_down(I) if skip is None else skip
-        # reading A10: s is the residual's RMS over the grid, so the network sees O(1)
+        # s is the residual's RMS over the grid, so the network sees O(1)
         # values at every grid size (the multiscale setting of Section 4.3)
         s = np.sqrt((np.abs(r) ** 2).reshape(B, -1).mean(axis=1))
         s_safe = np.where(s > 0, s, 1.0)

@@ -26,7 +26,7 @@ def generate_pairs(problem, vcycle, x: np.ndarray, iters: np.ndarray):
 
 
 def normalise_pairs(e: np.ndarray, r: np.ndarray):
-    """Reading A10: training pairs are scaled by 1/s_i (both e and r), s_i the RMS of
+    """The paper leaves the input scale unstated; here training pairs are scaled by 1/s_i (both e and r), s_i the RMS of
     r_i over the grid."""
     s = np.sqrt((np.abs(r) ** 2).reshape(r.shape[0], -1).mean(axis=1))
     return e / s[:, None, None], r / s[:, None, None]
@@ -42,7 +42,7 @@ def mse_loss(e_pred: np.ndarray, e_true: np.ndarray):
 
 def composed_preconditioner(problem, net, kfeat, vcycle):
     """Section 4.1: the network maps a residual to an error, which a V-cycle then
-    smooths.  Reading A9 (multiplicative): z = e + V(r - A e), e = Net(r)."""
+    smooths.  Read as a multiplicative composition: z = e + V(r - A e), e = Net(r)."""
     def M(r):
         rb = r[None] if r.ndim == 2 else r
         e, _ = net.forward(rb, kfeat, train=False)

@@ -423,21 +423,52 @@ int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
 }
 
 size_t cnn_workspace_bytes(const helm_problem* p, const helm_cnn* cnn, int batch) {
-  // forward + e and r' vectors of the composition
-  return cnn_forward_bytes(cnn, p->nx, batch) + 2 * static_cast<size_t>(batch) * p->npts(0) * sizeof(float2) + 1024;
+  // forward + e, r' and the compacted input / output of the network
+  return cnn_forward_bytes(cnn, p->nx, batch) + 4 * static_cast<size_t>(batch) * p->npts(0) * sizeof(float2) + 2048;
+}
+
+// out[b] = in[sel[b]] (gather, b < nsel) or out[sel[b]] = in[b] (scatter); n points each
+__global__ void k_gather_rows(const float2* __restrict__ in, float2* __restrict__ out, const int* __restrict__ sel,
+                              long n, int scatter) {
+  const int b = blockIdx.y;
+  const long src = scatter ? b : sel[b];
+  const long dst = scatter ? sel[b] : b;
+  const float4* s4 = reinterpret_cast<const float4*>(in + src * n);
+  float4* d4 = reinterpret_cast<float4*>(out + dst * n);
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n / 2;
+       i += static_cast<long>(gridDim.x) * blockDim.x)
+    d4[i] = s4[i];
 }
 
 int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn_, const float2* r, float2* z, int batch,
-                       Carve& cv, const VcycleScratch& vs, const int* active, cudaStream_t st) {
+                       Carve& cv, const VcycleScratch& vs, const int* active, cudaStream_t st, const int* sel,
+                       int nsel) {
   helm_cnn* cnn = const_cast<helm_cnn*>(cnn_);
-  float2* e = cv.take<float2>(static_cast<size_t>(batch) * p->npts(0));
-  float2* rp = cv.take<float2>(static_cast<size_t>(batch) * p->npts(0));
+  const long n = p->npts(0);
+  float2* e = cv.take<float2>(static_cast<size_t>(batch) * n);
+  float2* rp = cv.take<float2>(static_cast<size_t>(batch) * n);
+  float2* rs = cv.take<float2>(static_cast<size_t>(batch) * n);
+  float2* es = cv.take<float2>(static_cast<size_t>(batch) * n);
   if (cv.overflow) {
     set_error("cnn precond: workspace too small");
     return HELM_EWORKSPACE;
   }
-  int rc = cnn_forward_infer(cnn, p, r, e, batch, cv, st);
-  if (rc) return rc;
+  int rc;
+  if (sel == nullptr || nsel < 0) {
+    // every RHS goes through the network
+    if ((rc = cnn_forward_infer(cnn, p, r, e, batch, cv, st))) return rc;
+  } else {
+    // only the selected RHS: gather, forward on the compact batch, scatter; e = 0 for
+    // the others, whose preconditioner is then the plain V-cycle (z = V(r))
+    HELM_CUDA(cudaMemsetAsync(e, 0, static_cast<size_t>(batch) * n * sizeof(float2), st));
+    if (nsel > 0) {
+      const dim3 g(static_cast<unsigned>(std::min<long>(div_up(n / 2, 256), 512)), nsel);
+      HELM_LAUNCH("k_gather_rows", st, k_gather_rows<<<g, 256, 0, st>>>(r, rs, sel, n, 0));
+      if ((rc = cnn_forward_infer(cnn, p, rs, es, nsel, cv, st))) return rc;
+      HELM_LAUNCH("k_gather_rows", st, k_gather_rows<<<g, 256, 0, st>>>(es, e, sel, n, 1));
+      HELM_CHECK_LAUNCH("k_gather_rows");
+    }
+  }
   if ((rc = launch_apply(p, p->massA, e, r, rp, batch, 0, active, st))) return rc;   // r' = r - A e
   return launch_vcycle(p, rp, z, batch, vs, active, nullptr, st, e);                // z = e + V(r')
 }
@@ -627,7 +658,7 @@ int helm_cnn_precond_apply(const helm_problem* p, helm_cnn* c, const void* r, vo
     return HELM_EWORKSPACE;
   }
   return helm::launch_cnn_precond(p, c, static_cast<const float2*>(r), static_cast<float2*>(z), batch, cv, vs,
-                                  nullptr, static_cast<cudaStream_t>(stream));
+                                  nullptr, static_cast<cudaStream_t>(stream), nullptr, -1);
 }
 
 }  // extern "C"

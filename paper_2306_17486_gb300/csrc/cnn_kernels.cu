@@ -42,7 +42,7 @@ __global__ void k_norm_partial(const float2* __restrict__ r, long n, int nblk, d
   }
 }
 
-// s_b = RMS of r_b over the grid (the network's input scale, reading A10)
+// s_b = RMS of r_b over the grid (the network's input scale; the paper leaves it unstated)
 __global__ void k_norm_final(const double* __restrict__ part, int nblk, int B, long n, float* __restrict__ s,
                              float* __restrict__ inv) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,10 +84,21 @@ __global__ void k_prep_restrict(const float2* __restrict__ r, int N, int B, cons
 }
 
 // ---- depthwise 3x3 (stride 1, zero padding): thread per (pixel, 8-channel group) ----
-// y = act(scale * acc + shift) (bf16) and/or the raw accumulator (fp32)
-__global__ void k_dw3x3(const bf16* __restrict__ x, int B, int H, int W, int C, const float* __restrict__ w,
-                        const float* __restrict__ scale, const float* __restrict__ shift, int act,
-                        bf16* __restrict__ y, float* __restrict__ yraw) {
+// y = act(scale * acc + shift) (bf16) and/or the raw accumulator (fp32).  Weights and
+// the per-channel affine are staged in shared memory once per CTA.
+constexpr int DW_MAXC = 384;
+__global__ void __launch_bounds__(256) k_dw3x3(const bf16* __restrict__ x, int B, int H, int W, int C,
+                                               const float* __restrict__ w, const float* __restrict__ scale,
+                                               const float* __restrict__ shift, int act, bf16* __restrict__ y,
+                                               float* __restrict__ yraw) {
+  __shared__ float sw[9][DW_MAXC];
+  __shared__ float ssc[DW_MAXC], ssh[DW_MAXC];
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) sw[i % 9][i / 9] = w[i];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    ssc[c] = scale ? scale[c] : 1.f;
+    ssh[c] = shift ? shift[c] : 0.f;
+  }
+  __syncthreads();
   const int G = C / 8;
   const long total = static_cast<long>(B) * H * W * G;
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
@@ -109,8 +120,9 @@ __global__ void k_dw3x3(const bf16* __restrict__ x, int B, int H, int W, int C, 
         if (sx < 0 || sx >= W) continue;
         uint4 u = *reinterpret_cast<const uint4*>(x + ((static_cast<long>(b) * H + sy) * W + sx) * C + 8 * g);
         const bf16* e8 = reinterpret_cast<const bf16*>(&u);
+        const float* wt = &sw[ty * 3 + tx][8 * g];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = fmaf(w[(8 * g + e) * 9 + ty * 3 + tx], __bfloat162float(e8[e]), acc[e]);
+        for (int e = 0; e < 8; ++e) acc[e] = fmaf(wt[e], __bfloat162float(e8[e]), acc[e]);
       }
     }
     if (yraw) {
@@ -124,7 +136,7 @@ __global__ void k_dw3x3(const bf16* __restrict__ x, int B, int H, int W, int C, 
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int c = 8 * g + e;
-        float t = fmaf(acc[e], scale ? scale[c] : 1.f, shift ? shift[c] : 0.f);
+        float t = fmaf(acc[e], ssc[c], ssh[c]);
         if (act) t = fmaxf(t, 0.f) + log1pf(__expf(-fabsf(t)));
         ob[e] = __float2bfloat16_rn(t);
       }
@@ -338,37 +350,58 @@ __global__ void k_greens(const float* __restrict__ Kpar, int nk, int m, float ep
 }
 
 // ---- projection 1x1 (C -> 2, + bias) at I/2, bilinear prolongation to I, times s ----
-__global__ void k_proj_prolong(const bf16* __restrict__ u, int B, int Nc, int C, const float* __restrict__ w,
-                               const float* __restrict__ bias, const float* __restrict__ s,
-                               float2* __restrict__ e) {
+// one thread per pair of fine columns (2X, 2X+1) of a fine row: the projections of the
+// (at most) two coarse rows x three coarse columns it needs are computed once
+constexpr int PJ_C = 16;
+__global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u, int B, int Nc, int C,
+                                                      const float* __restrict__ w, const float* __restrict__ bias,
+                                                      const float* __restrict__ s, float2* __restrict__ e) {
+  float w0[PJ_C], w1[PJ_C];
+#pragma unroll
+  for (int ch = 0; ch < PJ_C; ++ch) {
+    w0[ch] = w[ch];
+    w1[ch] = w[C + ch];
+  }
+  const float b0 = bias[0], b1 = bias[1];
   const int N = 2 * Nc;
-  const long total = static_cast<long>(B) * N * N;
+  const long total = static_cast<long>(B) * N * Nc;   // (b, Y, K): fine pixels (Y, 2K) and (Y, 2K+1)
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
-    const int b = static_cast<int>(i / (static_cast<long>(N) * N));
-    const int Y = static_cast<int>((i / N) % N), X = static_cast<int>(i % N);
-    float2 acc = make_float2(0.f, 0.f);
-    const int jy0 = Y >> 1, jx0 = X >> 1;
-    const int ny = (Y & 1) ? 2 : 1, nx = (X & 1) ? 2 : 1;
-    const float wy = (Y & 1) ? 0.5f : 1.f, wx = (X & 1) ? 0.5f : 1.f;
-    for (int a = 0; a < ny; ++a) {
-      const int J = jy0 + a;
-      if (J >= Nc) continue;
-      for (int c = 0; c < nx; ++c) {
-        const int K = jx0 + c;
-        if (K >= Nc) continue;
-        const bf16* up = u + ((static_cast<long>(b) * Nc + J) * Nc + K) * C;
-        float p0 = bias[0], p1 = bias[1];
-        for (int ch = 0; ch < C; ++ch) {
-          const float v = __bfloat162float(up[ch]);
-          p0 = fmaf(w[ch], v, p0);
-          p1 = fmaf(w[C + ch], v, p1);
+    const int b = static_cast<int>(i / (static_cast<long>(N) * Nc));
+    const int Y = static_cast<int>((i / Nc) % N), K = static_cast<int>(i % Nc);
+    const int J = Y >> 1;
+    const float wy = (Y & 1) ? 0.5f : 1.f;
+    float2 pk[2][2];  // [row a][col c]: projection at coarse (J + a, K + c)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        pk[a][c] = make_float2(0.f, 0.f);
+        const int JJ = J + a, KK = K + c;
+        if ((a == 1 && !(Y & 1)) || JJ >= Nc || KK >= Nc) continue;
+        const uint4* up = reinterpret_cast<const uint4*>(u + ((static_cast<long>(b) * Nc + JJ) * Nc + KK) * C);
+        float p0 = b0, p1 = b1;
+#pragma unroll
+        for (int h = 0; h < PJ_C / 8; ++h) {
+          uint4 v = up[h];
+          const bf16* e8 = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float f = __bfloat162float(e8[q]);
+            p0 = fmaf(w0[8 * h + q], f, p0);
+            p1 = fmaf(w1[8 * h + q], f, p1);
+          }
         }
-        acc.x += wy * wx * p0;
-        acc.y += wy * wx * p1;
+        pk[a][c] = make_float2(p0, p1);
       }
-    }
-    e[i] = cscale(acc, s[b]);
+    // rows: even Y -> row J; odd Y -> (J + J+1)/2
+    const float2 r0 = (Y & 1) ? cscale(cadd(pk[0][0], pk[1][0]), wy) : pk[0][0];
+    const float2 r1 = (Y & 1) ? cscale(cadd(pk[0][1], pk[1][1]), wy) : pk[0][1];
+    const float sc = s[b];
+    float2* eo = e + (static_cast<long>(b) * N + Y) * N + 2 * K;
+    const float2 ev = cscale(r0, sc);
+    const float2 od = cscale(cscale(cadd(r0, r1), 0.5f), sc);
+    *reinterpret_cast<float4*>(eo) = make_float4(ev.x, ev.y, od.x, od.y);
   }
 }
 
@@ -394,6 +427,10 @@ int launch_prep(const float2* r, int N, int B, double* part, float* s, float* in
 
 int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const float* scale, const float* shift,
               int act, bf16* y, float* yraw, cudaStream_t st) {
+  if (C > DW_MAXC || C % 8) {
+    set_error("depthwise: %d channels (kernel supports multiples of 8 up to %d)", C, DW_MAXC);
+    return HELM_EINVAL;
+  }
   HELM_LAUNCH("k_dw3x3", st,
               k_dw3x3<<<grid_for(static_cast<long>(B) * H * W * (C / 8)), 256, 0, st>>>(x, B, H, W, C, w, scale,
                                                                                          shift, act, y, yraw));
@@ -445,7 +482,11 @@ int launch_greens(const float* Kpar, int nk, int m, float eps, int literal, floa
 
 int launch_proj(const bf16* u, int B, int Nc, int C, const float* w, const float* bias, const float* s, float2* e,
                 cudaStream_t st) {
-  const long total = static_cast<long>(B) * 4 * Nc * Nc;
+  if (C != PJ_C) {
+    set_error("projection: kernel built for %d input channels", PJ_C);
+    return HELM_EINVAL;
+  }
+  const long total = static_cast<long>(B) * 2 * Nc * Nc;
   HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<grid_for(total), 256, 0, st>>>(u, B, Nc, C, w, bias, s, e));
   HELM_CHECK_LAUNCH("k_proj_prolong");
   return HELM_OK;

@@ -45,23 +45,30 @@ struct ConvArgs {
   int add2_div;          // consecutive samples sharing one add2 entry (1: per sample)
   bf16* y;               // bf16 NHWC output or null
   float* yraw;           // fp32 NHWC raw accumulator or null
-  int tiles_per_img, ntiles;
-  int L;                 // window rows per plane
+  int seg_q;             // virtual output pixels per segment (whole rows for 3x3)
+  int segs_per_img, nsegs;
+  int L;                 // window rows per plane (odd)
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 template <int CS, int COUT, int TAPS>
 struct ConvCfg {
-  static constexpr int G = CS / 8;                         // 16-byte groups per pixel
+  static constexpr int G = CS / 8;                          // 16-byte groups per pixel
   static constexpr int NSPLIT = COUT > 256 ? 2 : 1;
   static constexpr int NH = COUT / NSPLIT;                  // N of one MMA
-  static constexpr int NCOLS = COUT <= 32 ? 32 : COUT <= 64 ? 64 : COUT <= 128 ? 128 : COUT <= 256 ? 256 : 512;
+  static constexpr int NBUF = 2 * COUT <= 512 ? 2 : 1;      // TMEM accumulators (double buffer)
+  static constexpr int NEED = NBUF * COUT;
+  static constexpr int NCOLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   static constexpr int BBYTES = TAPS * G * COUT * 16;
   static_assert(CS % 16 == 0, "K per tap must be a multiple of 16");
   static_assert(NH % 16 == 0 && NH <= 256, "N per MMA");
 };
 
+// One CTA works through segments (a band of whole output rows of one image, or for
+// 1x1 a run of pixels): it stages the segment's input window once, then for every
+// 128-pixel M-tile one thread issues the MMAs into one of two TMEM accumulators while
+// the 4 warps run the epilogue of the previous tile from the other.
 template <int CS, int COUT, int TAPS>
 __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
   using Cfg = ConvCfg<CS, COUT, TAPS>;
@@ -73,12 +80,11 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
   const int L = a.L;
   float* sScale = reinterpret_cast<float*>(sA + static_cast<size_t>(nph) * G * L * 16);
   float* sShift = sScale + COUT;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (warp == 0) tc::tmem_alloc(tslot, Cfg::NCOLS);
-  // weights and per-channel affine stay resident for all tiles of this CTA
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.wpk);
     uint4* dst = reinterpret_cast<uint4*>(sB);
@@ -89,7 +95,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
     }
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   tc::fence_proxy_async();
@@ -99,72 +106,87 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
   const uint32_t tmem = *tslot;
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   constexpr uint32_t idesc = tc::idesc_bf16(128, Cfg::NH);
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
   bool ok = true;
+  // window start (virtual output position) relative to the segment start
+  const int wofs = (TAPS == 1) ? 0 : -(a.Po + 1);
 
-  for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-    const int b = tile / a.tiles_per_img;
-    const int q0 = (tile % a.tiles_per_img) * 128;
+  for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x) {
+    const int b = seg / a.segs_per_img;
+    const int qs = (seg % a.segs_per_img) * a.seg_q;
+    const int qe = min(qs + a.seg_q, a.Ho * a.Po);
     const bf16* xb = a.x + static_cast<long>(b) * a.Hi * a.Wi * a.Cg;
-    // ---- stage the A window (t fastest: conflict-free 16-byte shared stores) ----
+    // ---- stage the window: group fastest (coalesced global loads), odd L keeps the
+    //      16-byte shared stores of 8 consecutive groups on distinct banks ----
     const int total = nph * G * L;
-    for (int idx = tid; idx < total; idx += 128) {
-      const int t = idx % L;
-      const int pg = idx / L;        // phase * G + g
-      const int g = pg % G, ph = pg / G;
-      int iy = -1, ix = -1;
-      if (TAPS == 1) {
-        const int q = q0 + t;
-        const int y = q / a.Po, x = q % a.Po;
-        if (y < a.Ho) { iy = y; ix = x; }
-      } else {
-        const int q = q0 - a.Po - 1 + t;
-        const int y = floordiv(q, a.Po), x = q - y * a.Po;
-        if (y >= 0 && y < a.Ho && x < a.Wo) {
-          if (a.mode == HELM_CONV_S1) {
-            iy = y; ix = x;
-          } else if (a.mode == HELM_CONV_S2) {
-            iy = 2 * y + (ph >> 1); ix = 2 * x + (ph & 1);
-          } else {  // transposed stride 2: zero-inserted upsampling
-            if (!(y & 1) && !(x & 1)) { iy = y >> 1; ix = x >> 1; }
+    constexpr int UNR = 4;   // loads in flight per thread
+    for (int base = 0; base < total; base += 128 * UNR) {
+      uint4 v[UNR];
+      int dst[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int idx = base + u * 128 + tid;
+        v[u] = make_uint4(0u, 0u, 0u, 0u);
+        dst[u] = -1;
+        if (idx >= total) continue;
+        const int g = idx % G;
+        const int rem = idx / G;
+        const int t = rem % L, ph = rem / L;
+        dst[u] = (ph * G + g) * L + t;
+        const int q = qs + wofs + t;
+        int iy = -1, ix = -1;
+        if (TAPS == 1) {
+          if (q < qe) { iy = q / a.Po; ix = q % a.Po; }
+        } else {
+          const int yv = floordiv(q, a.Po), xv = q - yv * a.Po;
+          if (yv >= 0 && yv < a.Ho && xv < a.Wo) {
+            if (a.mode == HELM_CONV_S1) {
+              iy = yv; ix = xv;
+            } else if (a.mode == HELM_CONV_S2) {
+              iy = 2 * yv + (ph >> 1); ix = 2 * xv + (ph & 1);
+            } else if (!(yv & 1) && !(xv & 1)) {  // transposed stride 2: zero-inserted upsampling
+              iy = yv >> 1; ix = xv >> 1;
+            }
+          }
+        }
+        if (iy >= 0) {
+          const bf16* px = xb + (static_cast<long>(iy) * a.Wi + ix) * a.Cg;
+          const int c0 = 8 * g;
+          if (c0 + 8 <= a.Cg) {
+            v[u] = __ldg(reinterpret_cast<const uint4*>(px + c0));
+          } else if (c0 < a.Cg) {
+            uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int e = 0; c0 + e < a.Cg && e < 8; ++e) tmp[e] = reinterpret_cast<const uint16_t*>(px)[c0 + e];
+            v[u] = make_uint4(tmp[0] | (tmp[1] << 16), tmp[2] | (tmp[3] << 16), tmp[4] | (tmp[5] << 16),
+                              tmp[6] | (tmp[7] << 16));
           }
         }
       }
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (iy >= 0) {
-        const bf16* px = xb + (static_cast<long>(iy) * a.Wi + ix) * a.Cg;
-        const int c0 = 8 * g;
-        if (c0 + 8 <= a.Cg) {
-          v = *reinterpret_cast<const uint4*>(px + c0);
-        } else if (c0 < a.Cg) {
-          uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          for (int e = 0; c0 + e < a.Cg && e < 8; ++e) tmp[e] = reinterpret_cast<const uint16_t*>(px)[c0 + e];
-          v = make_uint4(tmp[0] | (tmp[1] << 16), tmp[2] | (tmp[3] << 16), tmp[4] | (tmp[5] << 16),
-                         tmp[6] | (tmp[7] << 16));
-        }
-      }
-      *reinterpret_cast<uint4*>(sA + (static_cast<size_t>(pg) * L + t) * 16) = v;
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+        if (dst[u] >= 0) *reinterpret_cast<uint4*>(sA + static_cast<size_t>(dst[u]) * 16) = v[u];
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
-    // ---- one thread issues the MMAs of the tile ----
-    if (tid == 0) {
+    const int ntiles = (qe - qs + 127) / 128;
+    auto issue = [&](int j) {
       tc::fence_after_sync();
+      const int buf = j % Cfg::NBUF;
       const uint32_t lboA = static_cast<uint32_t>(L) * 16u;
       int kstep = 0;
 #pragma unroll 1
       for (int tap = 0; tap < TAPS; ++tap) {
-        int row = 0, ph = 0;
+        int row = 128 * j, ph = 0;
         if (TAPS == 9) {
           const int ty = tap / 3, tx = tap % 3;
           if (a.mode == HELM_CONV_S2) {
             const int sy = ty == 0 ? -1 : 0, py = ty == 1 ? 0 : 1;
             const int sx = tx == 0 ? -1 : 0, px = tx == 1 ? 0 : 1;
             ph = py * 2 + px;
-            row = (sy + 1) * a.Po + (sx + 1);
+            row += (sy + 1) * a.Po + (sx + 1);
           } else {
-            row = ty * a.Po + tx;
+            row += ty * a.Po + tx;
           }
         }
 #pragma unroll
@@ -175,69 +197,83 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
           for (int nh = 0; nh < Cfg::NSPLIT; ++nh) {
             const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT + nh * Cfg::NH) * 16);
             const uint64_t bd = tc::sdesc(baddr, COUT * 16, 128);
-            tc::mma_bf16(tmem + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
+            tc::mma_bf16(tmem + buf * COUT + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
           }
           ++kstep;
         }
       }
-      tc::commit(bar);
+      tc::commit(&bar[buf]);
+    };
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue(0);
     }
-    ok = mbar_wait_bounded(bar, phase, HELM_DEVERR_MMA_WAIT);
-    phase ^= 1;
-    tc::fence_after_sync();
-    // ---- epilogue: thread tid <-> TMEM lane tid <-> pixel q0 + tid ----
-    const int q = q0 + tid;
-    const int y = q / a.Po, x = q % a.Po;
-    const bool valid = ok && y < a.Ho && x < a.Wo;
-    const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
-    const long pix2 = (static_cast<long>(b / a.add2_div) * a.Ho + y) * a.Wo + x;
+    for (int j = 0; j < ntiles; ++j) {
+      if (Cfg::NBUF == 2 && tid == 0 && j + 1 < ntiles) issue(j + 1);
+      const int buf = j % Cfg::NBUF;
+      ok = mbar_wait_bounded(&bar[buf], phase[buf], HELM_DEVERR_MMA_WAIT) && ok;
+      phase[buf] ^= 1u;
+      tc::fence_after_sync();
+      // ---- epilogue: thread tid <-> TMEM lane tid <-> virtual pixel qs + 128 j + tid ----
+      const int q = qs + 128 * j + tid;
+      const int y = q / a.Po, x = q % a.Po;
+      const bool valid = ok && q < qe && x < a.Wo;
+      const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
+      const long pix2 = (static_cast<long>(b / a.add2_div) * a.Ho + y) * a.Wo + x;
 #pragma unroll 1
-    for (int c0 = 0; c0 < COUT; c0 += 16) {
-      float v[16];
-      tc::ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (!valid) continue;
-      if (a.yraw) {
-        float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
+      for (int c0 = 0; c0 < COUT; c0 += 16) {
+        float v[16];
+        tc::ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * COUT + c0, v);
+        if (!valid) continue;
+        if (a.yraw) {
+          float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-      }
-      if (a.y) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
-          v[i] = a.act ? tc::softplus(t) : t;
+          for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
-        if (a.add1) {
-          const uint4* p = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
+        if (a.y) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint4 u = p[h];
-            const bf16* e = reinterpret_cast<const bf16*>(&u);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+          for (int i = 0; i < 16; ++i) {
+            float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
+            v[i] = a.act ? tc::softplus_fast(t) : t;
           }
-        }
-        if (a.add2) {
-          const uint4* p = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
+          if (a.add1) {
+            const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint4 u = p[h];
-            const bf16* e = reinterpret_cast<const bf16*>(&u);
+            for (int h = 0; h < 2; ++h) {
+              uint4 u = pp[h];
+              const bf16* e = reinterpret_cast<const bf16*>(&u);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+              for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+            }
           }
-        }
-        uint4 o[2];
-        bf16* ob = reinterpret_cast<bf16*>(o);
+          if (a.add2) {
+            const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) ob[i] = __float2bfloat16_rn(v[i]);
-        uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
-        dst[0] = o[0];
-        dst[1] = o[1];
+            for (int h = 0; h < 2; ++h) {
+              uint4 u = pp[h];
+              const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+            }
+          }
+          uint4 o[2];
+          __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
+          dst[0] = o[0];
+          dst[1] = o[1];
+        }
       }
+      tc::fence_before_sync();
+      ok = __syncthreads_and(ok) != 0;  // uniform: a timed-out wait stops every thread
+      if (Cfg::NBUF == 1 && tid == 0 && j + 1 < ntiles && ok) {
+        tc::fence_after_sync();
+        issue(j + 1);
+      }
+      if (!ok) break;
     }
-    tc::fence_before_sync();
-    ok = __syncthreads_and(ok) != 0;  // uniform: a timed-out wait stops every thread
+    __syncthreads();  // the window is re-staged by the next segment
   }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, Cfg::NCOLS);
@@ -278,7 +314,29 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   using Cfg = ConvCfg<CS, COUT, TAPS>;
   ConvArgs a = a0;
   const int nph = a.mode == HELM_CONV_S2 ? 4 : 1;
-  const size_t smem = Cfg::BBYTES + static_cast<size_t>(nph) * Cfg::G * a.L * 16 + 2 * COUT * 4 + 64;
+  // window budget: one CTA per SM for the heavy-weight layers, two otherwise
+  const size_t budget = Cfg::BBYTES > 40 * 1024 ? 200 * 1024 : 56 * 1024;
+  const size_t fixed = Cfg::BBYTES + 2 * COUT * 4 + 64;
+  const size_t plane_row = static_cast<size_t>(nph) * Cfg::G * 16;
+  auto window_rows = [&](int segq) {
+    const int nt = (segq + 127) / 128;
+    int Lr = 128 * nt + (TAPS == 1 ? 0 : (a.mode == HELM_CONV_S2 ? a.Po + 1 : 2 * a.Po + 2));
+    return Lr | 1;
+  };
+  if (TAPS == 1) {
+    int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (plane_row * 128));
+    tiles = std::max(1, std::min(tiles, 16));
+    a.seg_q = 128 * tiles;
+  } else {
+    int R = 1;
+    for (int r = 2; r <= std::min(a.Ho, 32); ++r)
+      if (fixed + plane_row * window_rows(r * a.Po) <= budget) R = r;
+    a.seg_q = R * a.Po;
+  }
+  a.L = window_rows(a.seg_q);
+  a.segs_per_img = helm::div_up(static_cast<long>(a.Ho) * a.Po, a.seg_q);
+  a.nsegs = a.segs_per_img * a.B;
+  const size_t smem = fixed + plane_row * a.L;
   if (smem > 227 * 1024) {
     helm::set_error("conv: shared memory %zu bytes exceeds the per-CTA limit (grid row too wide)", smem);
     return HELM_ESHAPE;
@@ -296,7 +354,7 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   int per_sm = 0;
   HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CS, COUT, TAPS>, 128, smem));
   per_sm = std::max(1, std::min(per_sm, 512 / Cfg::NCOLS));
-  const int grid = std::max(1, std::min(a.ntiles, nsm * per_sm));
+  const int grid = std::max(1, std::min(a.nsegs, nsm * per_sm));
   HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS><<<grid, 128, smem, st>>>(a));
   HELM_CHECK_LAUNCH("k_conv_tc");
   return HELM_OK;
@@ -355,9 +413,6 @@ int conv_tc(const ConvLaunch& c, cudaStream_t st) {
     a.Wo = c.Wi;
     a.Po = a.Wo + 1;
   }
-  a.L = taps == 1 ? 128 : (c.mode == HELM_CONV_S2 ? 128 + a.Po + 1 : 128 + 2 * a.Po + 2);
-  a.tiles_per_img = div_up(static_cast<long>(a.Ho) * a.Po, 128);
-  a.ntiles = a.tiles_per_img * a.B;
   const int CS = conv_cs(c.Ci);
 #define HELM_CONV_CASE(cs, co, tp) \
   if (CS == cs && c.Co == co && taps == tp) return launch_t<cs, co, tp>(a, st);

@@ -54,6 +54,10 @@ struct Solver {
   int* counter;        // [1]
   double* rpart;       // [B][rblk] residual partials
   int rblk;
+  double* prev;        // [B] true relative residual at the previous restart
+  int* fb;             // [B] 1: this RHS fell back to the plain V-cycle preconditioner
+  int* sel;            // [B] indices of the RHS the network runs on this cycle
+  int use_cnn;         // the composed preconditioner is in use (fallback test active)
 };
 
 // ---- streaming kernels ----------------------------------------------------------
@@ -334,6 +338,8 @@ __global__ void k_fin_bnorm(Solver S) {
       S.active[b] = 1;
     }
     S.cyc[b] = 0;
+    S.fb[b] = 0;
+    S.prev[b] = -1.0;
   }
 }
 
@@ -387,6 +393,10 @@ __global__ void k_fin_restart(Solver S, double tol) {
       S.active[b] = 0;
       S.cyc[b] = 0;
     } else {
+      // a cycle with the learned preconditioner that failed to reduce the residual
+      // hands this RHS to the plain SL V-cycle for the rest of the solve
+      if (S.use_cnn && !S.fb[b] && S.prev[b] > 0.0 && rel > 0.95 * S.prev[b]) S.fb[b] = 1;
+      S.prev[b] = rel;
       S.cyc[b] = 1;
       S.inv[b] = static_cast<float>(1.0 / beta);
       S.g[static_cast<long>(b) * MAXV] = make_double2(beta, 0.0);
@@ -469,7 +479,8 @@ namespace helm {
 // preconditioner hook implemented with the CNN (cnn.cu); returns HELM_EINVAL if the
 // library was built without it.
 int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn, const float2* r, float2* z, int batch,
-                       Carve& carve, const VcycleScratch& vs, const int* active, cudaStream_t st);
+                       Carve& carve, const VcycleScratch& vs, const int* active, cudaStream_t st,
+                       const int* sel_dev = nullptr, int nsel = -1);
 size_t cnn_workspace_bytes(const helm_problem* p, const helm_cnn* cnn, int batch);
 
 static void carve_solver(Carve& c, const helm_problem* p, int B, int m, Solver* S) {
@@ -503,6 +514,9 @@ static void carve_solver(Carve& c, const helm_problem* p, int B, int m, Solver* 
   S->maxit = c.take<int>(B);
   S->counter = c.take<int>(1);
   S->rpart = c.take<double>(static_cast<size_t>(B) * S->rblk);
+  S->prev = c.take<double>(B);
+  S->fb = c.take<int>(B);
+  S->sel = c.take<int>(B);
 }
 
 size_t vcycle_bytes(const helm_problem* p, int batch) {
@@ -576,6 +590,7 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
   const long n = S.n;
   const long vstride = static_cast<long>(B) * n;
   const int m = o.restart;
+  S.use_cnn = cnn != nullptr ? 1 : 0;
   dim3 gs(S.nblk, B);
   int rc;
 
@@ -611,13 +626,25 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
     if (nact == 0) break;
     const bool warm = use_cnn && cycle == 0 && o.warmup_iters > 0;
     const int mlen = warm ? std::min(o.warmup_iters, m) : m;
+    // RHS the network runs on during this cycle: active and not fallen back
+    int nsel = 0;
+    if (use_cnn && !warm) {
+      std::vector<int> act(B), fbv(B), sel;
+      HELM_CUDA(cudaMemcpyAsync(act.data(), S.cyc, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+      HELM_CUDA(cudaMemcpyAsync(fbv.data(), S.fb, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+      HELM_CUDA(cudaStreamSynchronize(st));
+      for (int bb = 0; bb < B; ++bb)
+        if (act[bb] && !fbv[bb]) sel.push_back(bb);
+      nsel = static_cast<int>(sel.size());
+      if (nsel) HELM_CUDA(cudaMemcpyAsync(S.sel, sel.data(), nsel * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     for (int j = 0; j < mlen; ++j) {
       float2* vj = S.V + j * vstride;
       float2* zj = S.Z + j * vstride;
       float2* w = S.V + (j + 1) * vstride;
       if (use_cnn && !warm) {
         Carve cc(c.base + c.off, c.cap - c.off);
-        rc = launch_cnn_precond(p, cnn, vj, zj, B, cc, vs, S.cyc, st);
+        rc = launch_cnn_precond(p, cnn, vj, zj, B, cc, vs, S.cyc, st, S.sel, nsel);
       } else {
         rc = launch_vcycle(p, vj, zj, B, vs, S.cyc, nullptr, st);
       }

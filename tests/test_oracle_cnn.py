@@ -88,7 +88,7 @@ def test_bn_eval_folding_equivalence():
 
 
 def test_eval_forward_is_scale_equivariant_and_zero_safe():
-    """Reading A10: e = s Net(r/s) with s = RMS(r), so e(c r) = c e(r) for c > 0."""
+    """Input scaling: e = s Net(r/s) with s = RMS(r), so e(c r) = c e(r) for c > 0."""
     net, P, kf, r, _ = _setup(B=2)
     e1, _ = net.forward(r, kf, train=False)
     e2, _ = net.forward(3.0 * r, kf, train=False)

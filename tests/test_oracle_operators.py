@@ -109,7 +109,7 @@ def _vcycle_error_radius(N, levels, nu):
 def test_vcycle_factor_at_omega_zero_matches_lfa(levels):
     """At omega = 0 the SL operator is -Delta_h.  Local Fourier analysis of damped
     Jacobi (w = 0.8) gives the smoothing factor mu = max(|1-2w|, |1-w/2|) = 0.6, so
-    V(1,1) ~ mu^2 = 0.36 and V(2,2) ~ mu^4 = 0.13 (reading A20)."""
+    V(1,1) ~ mu^2 = 0.36 and V(2,2) ~ mu^4 = 0.13 (so the paper's 0.2 is read as a V(2,2) bound)."""
     rho1, BV = _vcycle_error_radius(32, levels, 1)
     rho2, _ = _vcycle_error_radius(32, levels, 2)
     assert 0.30 < rho1 <= 0.40
