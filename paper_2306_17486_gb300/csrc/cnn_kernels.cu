@@ -145,6 +145,100 @@ __global__ void __launch_bounds__(256) k_dw3x3(const bf16* __restrict__ x, int B
   }
 }
 
+// Depthwise 3x3 for the expanded widths of the inverted bottlenecks (C = 6 c), one CTA
+// per output row: thread (strip, g) holds the 72 weights of channel group g in registers
+// and slides along a strip of DW_XS pixels, so each input vector is loaded once per
+// row of taps and reused by up to three outputs.
+constexpr int DW_XS = 4;
+template <int C>
+__global__ void __launch_bounds__(256) k_dw3x3_row(const bf16* __restrict__ x, int H, int W,
+                                                   const float* __restrict__ w, const float* __restrict__ scale,
+                                                   const float* __restrict__ shift, int act, bf16* __restrict__ y,
+                                                   float* __restrict__ yraw) {
+  constexpr int G = C / 8;
+  __shared__ float4 sw[9][C / 4];
+  __shared__ float ssc[C], ssh[C];
+  float* swf = reinterpret_cast<float*>(sw);
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) swf[(i % 9) * C + i / 9] = w[i];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    ssc[c] = scale ? scale[c] : 1.f;
+    ssh[c] = shift ? shift[c] : 0.f;
+  }
+  __syncthreads();
+  const int row = blockIdx.y;                 // b * H + yy
+  const int yy = row % H;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nstrip = (W + DW_XS - 1) / DW_XS;
+  if (t >= nstrip * G) return;
+  const int g = t % G, x0 = (t / G) * DW_XS;
+  float wr[9][8];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float4 lo = sw[k][2 * g], hi = sw[k][2 * g + 1];
+    wr[k][0] = lo.x; wr[k][1] = lo.y; wr[k][2] = lo.z; wr[k][3] = lo.w;
+    wr[k][4] = hi.x; wr[k][5] = hi.y; wr[k][6] = hi.z; wr[k][7] = hi.w;
+  }
+  float acc[DW_XS][8];
+#pragma unroll
+  for (int o = 0; o < DW_XS; ++o)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[o][e] = 0.f;
+#pragma unroll
+  for (int ty = 0; ty < 3; ++ty) {
+    const int sy = yy + ty - 1;
+    if (sy < 0 || sy >= H) continue;
+    const bf16* rp = x + (static_cast<long>(row + ty - 1) * W) * C + 8 * g;
+#pragma unroll
+    for (int c = 0; c < DW_XS + 2; ++c) {
+      const int sx = x0 + c - 1;
+      if (sx < 0 || sx >= W) continue;
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(rp + static_cast<long>(sx) * C));
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+      float f[8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 v = __bfloat1622float2(h2[e]);
+        f[2 * e] = v.x;
+        f[2 * e + 1] = v.y;
+      }
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) {
+        const int o = c - tx;   // output strip position that this tap of this column feeds
+        if (o < 0 || o >= DW_XS) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[o][e] = fmaf(wr[ty * 3 + tx][e], f[e], acc[o][e]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < DW_XS; ++o) {
+    const int xx = x0 + o;
+    if (xx >= W) break;
+    const long pix = static_cast<long>(row) * W + xx;
+    if (yraw) {
+      float4* op = reinterpret_cast<float4*>(yraw + pix * C + 8 * g);
+      op[0] = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+      op[1] = make_float4(acc[o][4], acc[o][5], acc[o][6], acc[o][7]);
+    }
+    if (y) {
+      uint4 u;
+      __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 8 * g + 2 * e;
+        float t0 = fmaf(acc[o][2 * e], ssc[c], ssh[c]);
+        float t1 = fmaf(acc[o][2 * e + 1], ssc[c + 1], ssh[c + 1]);
+        if (act) {
+          t0 = fmaxf(t0, 0.f) + __logf(1.f + __expf(-fabsf(t0)));
+          t1 = fmaxf(t1, 0.f) + __logf(1.f + __expf(-fabsf(t1)));
+        }
+        ob[e] = __floats2bfloat162_rn(t0, t1);
+      }
+      *reinterpret_cast<uint4*>(y + pix * C + 8 * g) = u;
+    }
+  }
+}
+
 // ---- implicit layer (Eq. 14), one CTA per (sample, complex channel) -----------------
 // x: channels k (Re) and k + C/2 (Im) of an m x m map; zero-pad to 2m x 2m, DFT,
 // multiply by G_hat_k, inverse DFT, keep the top-left m x m block.  The DFTs are
@@ -431,6 +525,20 @@ int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const f
     set_error("depthwise: %d channels (kernel supports multiples of 8 up to %d)", C, DW_MAXC);
     return HELM_EINVAL;
   }
+  const int nstrip = div_up(W, DW_XS);
+#define HELM_DW_CASE(cc)                                                                                   \
+  if (C == cc) {                                                                                         \
+    dim3 grid(div_up(nstrip * (cc / 8), 256), B * H);                                                    \
+    HELM_LAUNCH("k_dw3x3", st, k_dw3x3_row<cc><<<grid, 256, 0, st>>>(x, H, W, w, scale, shift, act, y, yraw)); \
+    HELM_CHECK_LAUNCH("k_dw3x3");                                                                        \
+    return HELM_OK;                                                                                      \
+  }
+  if (static_cast<long>(B) * H <= 65535) {
+    HELM_DW_CASE(96)
+    HELM_DW_CASE(192)
+    HELM_DW_CASE(384)
+  }
+#undef HELM_DW_CASE
   HELM_LAUNCH("k_dw3x3", st,
               k_dw3x3<<<grid_for(static_cast<long>(B) * H * W * (C / 8)), 256, 0, st>>>(x, B, H, W, C, w, scale,
                                                                                          shift, act, y, yraw));

@@ -17,8 +17,8 @@
 //   transposed s2 : the zero-inserted upsampling up(2y, 2x) = in(y, x) at output
 //                   resolution, with the kernel flipped (dy -> 1 - ky)
 //   1x1           : 128 consecutive pixels, Po = Wo
-// One thread issues all MMAs of a tile and commits them to an mbarrier; 4 warps read
-// the accumulator with tcgen05.ld (thread t = pixel q0 + t) and run the epilogue.
+// One thread issues all MMAs of a tile and commits them to an mbarrier; 8 warps read
+// the accumulator with tcgen05.ld (TMEM lane t = pixel q0 + t) and run the epilogue.
 // CTAs are persistent over tiles; weights stay resident in shared memory.
 #include <cuda_bf16.h>
 
@@ -65,12 +65,16 @@ struct ConvCfg {
   static_assert(NH % 16 == 0 && NH <= 256, "N per MMA");
 };
 
-// One CTA works through segments (a band of whole output rows of one image, or for
-// 1x1 a run of pixels): it stages the segment's input window once, then for every
+// One CTA (8 warps) works through segments (a band of whole output rows of one image,
+// or for 1x1 a run of pixels): it stages the segment's input window once with
+// asynchronous 16-byte copies (zero-filled outside the image), then for every
 // 128-pixel M-tile one thread issues the MMAs into one of two TMEM accumulators while
-// the 4 warps run the epilogue of the previous tile from the other.
+// the warps run the epilogue of the previous tile from the other.  Warps w and w + 4
+// share TMEM lanes 32 (w mod 4) .. + 31 and split the output channels in 16-wide chunks.
+constexpr int CONV_THREADS = 256;
+
 template <int CS, int COUT, int TAPS>
-__global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   using Cfg = ConvCfg<CS, COUT, TAPS>;
   constexpr int G = Cfg::G;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -83,13 +87,14 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));   // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int lane_q = warp & 3, chalf = warp >> 2;
 
   if (warp == 0) tc::tmem_alloc(tslot, Cfg::NCOLS);
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.wpk);
     uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < Cfg::BBYTES / 16; i += 128) dst[i] = src[i];
-    for (int c = tid; c < COUT; c += 128) {
+    for (int i = tid; i < Cfg::BBYTES / 16; i += CONV_THREADS) dst[i] = src[i];
+    for (int c = tid; c < COUT; c += CONV_THREADS) {
       sScale[c] = a.scale ? a.scale[c] : 1.f;
       sShift[c] = a.shift ? a.shift[c] : 0.f;
     }
@@ -110,33 +115,23 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
   bool ok = true;
   // window start (virtual output position) relative to the segment start
   const int wofs = (TAPS == 1) ? 0 : -(a.Po + 1);
+  const bool full_groups = (a.Cg % 8) == 0;
 
   for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x) {
     const int b = seg / a.segs_per_img;
     const int qs = (seg % a.segs_per_img) * a.seg_q;
     const int qe = min(qs + a.seg_q, a.Ho * a.Po);
     const bf16* xb = a.x + static_cast<long>(b) * a.Hi * a.Wi * a.Cg;
-    // ---- stage the window: group fastest (coalesced global loads), odd L keeps the
-    //      16-byte shared stores of 8 consecutive groups on distinct banks ----
-    const int total = nph * G * L;
-    constexpr int UNR = 4;   // loads in flight per thread
-    for (int base = 0; base < total; base += 128 * UNR) {
-      uint4 v[UNR];
-      int dst[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int idx = base + u * 128 + tid;
-        v[u] = make_uint4(0u, 0u, 0u, 0u);
-        dst[u] = -1;
-        if (idx >= total) continue;
-        const int g = idx % G;
-        const int rem = idx / G;
-        const int t = rem % L, ph = rem / L;
-        dst[u] = (ph * G + g) * L + t;
+    // ---- stage the window: group fastest (coalesced global reads); plane (ph, g)
+    //      holds L rows of 16 bytes ----
+    for (int ph = 0; ph < nph; ++ph) {
+      const int total = G * L;
+      for (int idx = tid; idx < total; idx += CONV_THREADS) {
+        const int g = idx % G, t = idx / G;
         const int q = qs + wofs + t;
-        int iy = -1, ix = -1;
+        int iy = -1, ix = 0;
         if (TAPS == 1) {
-          if (q < qe) { iy = q / a.Po; ix = q % a.Po; }
+          if (q < qe) { iy = 0; ix = q; }   // 1x1: the virtual pixel is the linear pixel
         } else {
           const int yv = floordiv(q, a.Po), xv = q - yv * a.Po;
           if (yv >= 0 && yv < a.Ho && xv < a.Wo) {
@@ -149,23 +144,21 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
             }
           }
         }
-        if (iy >= 0) {
-          const bf16* px = xb + (static_cast<long>(iy) * a.Wi + ix) * a.Cg;
-          const int c0 = 8 * g;
-          if (c0 + 8 <= a.Cg) {
-            v[u] = __ldg(reinterpret_cast<const uint4*>(px + c0));
-          } else if (c0 < a.Cg) {
-            uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int c0 = 8 * g;
+        uint8_t* dptr = sA + static_cast<size_t>((ph * G + g) * L + t) * 16;
+        const bf16* px = xb + (static_cast<long>(iy < 0 ? 0 : iy) * a.Wi + ix) * a.Cg;
+        if (full_groups) {
+          tc::cp_async16(smem_u32(dptr), iy >= 0 ? px + c0 : xb, iy >= 0 ? 16u : 0u);
+        } else {
+          uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          if (iy >= 0)
             for (int e = 0; c0 + e < a.Cg && e < 8; ++e) tmp[e] = reinterpret_cast<const uint16_t*>(px)[c0 + e];
-            v[u] = make_uint4(tmp[0] | (tmp[1] << 16), tmp[2] | (tmp[3] << 16), tmp[4] | (tmp[5] << 16),
-                              tmp[6] | (tmp[7] << 16));
-          }
+          *reinterpret_cast<uint4*>(dptr) = make_uint4(tmp[0] | (tmp[1] << 16), tmp[2] | (tmp[3] << 16),
+                                                       tmp[4] | (tmp[5] << 16), tmp[6] | (tmp[7] << 16));
         }
       }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-        if (dst[u] >= 0) *reinterpret_cast<uint4*>(sA + static_cast<size_t>(dst[u]) * 16) = v[u];
     }
+    tc::cp_async_wait_all();
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -214,16 +207,16 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a) {
       ok = mbar_wait_bounded(&bar[buf], phase[buf], HELM_DEVERR_MMA_WAIT) && ok;
       phase[buf] ^= 1u;
       tc::fence_after_sync();
-      // ---- epilogue: thread tid <-> TMEM lane tid <-> virtual pixel qs + 128 j + tid ----
-      const int q = qs + 128 * j + tid;
-      const int y = q / a.Po, x = q % a.Po;
+      // ---- epilogue: TMEM lane (tid mod 128) <-> virtual pixel qs + 128 j + lane ----
+      const int q = qs + 128 * j + (tid & 127);
+      const int y = q / a.Po, x = q - y * a.Po;
       const bool valid = ok && q < qe && x < a.Wo;
       const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
       const long pix2 = (static_cast<long>(b / a.add2_div) * a.Ho + y) * a.Wo + x;
 #pragma unroll 1
-      for (int c0 = 0; c0 < COUT; c0 += 16) {
+      for (int c0 = 16 * chalf; c0 < COUT; c0 += 32) {
         float v[16];
-        tc::ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * COUT + c0, v);
+        tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * COUT + c0, v);
         if (!valid) continue;
         if (a.yraw) {
           float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
@@ -352,10 +345,10 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     attr = true;
   }
   int per_sm = 0;
-  HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CS, COUT, TAPS>, 128, smem));
+  HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CS, COUT, TAPS>, CONV_THREADS, smem));
   per_sm = std::max(1, std::min(per_sm, 512 / Cfg::NCOLS));
   const int grid = std::max(1, std::min(a.nsegs, nsm * per_sm));
-  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS><<<grid, 128, smem, st>>>(a));
+  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS><<<grid, CONV_THREADS, smem, st>>>(a));
   HELM_CHECK_LAUNCH("k_conv_tc");
   return HELM_OK;
 }
