@@ -134,6 +134,27 @@ int helm_helmholtz_residual_fp64(const helm_problem* p, const void* b, const voi
 int helm_slmg_vcycle(const helm_problem* p, const void* r, void* z, int batch, void* ws, size_t ws_bytes,
                      void* stream);
 
+/*
+ * z = V(r) exactly as helm_slmg_vcycle, without a workspace argument: the scratch is a
+ * fixed device array inside the library of HELM_VCYCLE_STATIC_BYTES (16 MiB), resident
+ * on every device the library is loaded on.  The paper has no counterpart: it is for
+ * callers that cannot pass or allocate scratch (e.g. a preconditioner callback of an
+ * external Krylov solver).  The call allocates nothing.
+ *   - Scratch need per call: the V-cycle's coarse-level buffers for `batch` RHS, about
+ *     2.2 MB per RHS at 576^2 with 4 levels (7 RHS fit).  A call that needs more
+ *     returns HELM_EWORKSPACE before launching anything.
+ *   - Nothing in the scratch has to start at zero: every element is written before it
+ *     is read within one call.
+ *   - The first call on a device looks up the array's address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - All calls on one device share the one array: calls that may overlap in time
+ *     (different streams, or threads without ordering) race on it.  Order them on one
+ *     stream.
+ *   - The current device must be the problem's device (else HELM_EINVAL).
+ */
+#define HELM_VCYCLE_STATIC_BYTES ((size_t)16 << 20)
+int helm_slmg_vcycle_static(const helm_problem* p, const void* r, void* z, int batch, void* stream);
+
 /* FGMRES options. */
 typedef struct {
   int restart;      /* FGMRES(m) restart length (paper: 10)                                */

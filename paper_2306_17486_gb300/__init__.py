@@ -130,6 +130,17 @@ def slmg_vcycle(p: Problem, r: torch.Tensor, z: torch.Tensor | None = None) -> t
     return z
 
 
+def slmg_vcycle_static(p: Problem, r: torch.Tensor, z: torch.Tensor | None = None) -> torch.Tensor:
+    """z = V(r) like slmg_vcycle, using the library's fixed device scratch instead of a
+    workspace (for callers that cannot allocate); raises if the batch needs more scratch
+    than the library holds."""
+    _need(r, torch.complex64, "r")
+    z = torch.empty_like(r) if z is None else z
+    B = r.shape[0] if r.dim() == 3 else 1
+    check(lib().helm_slmg_vcycle_static(p.handle, _ptr(r), _ptr(z), B, _stream()), "helm_slmg_vcycle_static")
+    return z
+
+
 def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn=None, restart=10, rtol=1e-6,
                  maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None):
     """Solve h^2 A x = b (b complex64 [B, ny, nx]); x complex128 (in: x0, out: solution).

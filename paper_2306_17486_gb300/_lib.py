@@ -47,6 +47,7 @@ PROTOS = {
     "helm_helmholtz_apply": (i32, [vp, vp, vp, i32, vp]),
     "helm_helmholtz_residual_fp64": (i32, [vp, vp, vp, vp, vp, i32, vp, sz, vp]),
     "helm_slmg_vcycle": (i32, [vp, vp, vp, i32, vp, sz, vp]),
+    "helm_slmg_vcycle_static": (i32, [vp, vp, vp, i32, vp]),
     "helm_fgmres_opts_default": (None, [C.POINTER(FgmresOpts)]),
     "helm_fgmres_solve": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, vp, vp, sz, vp]),
     "helm_datagen_pairs": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]),
