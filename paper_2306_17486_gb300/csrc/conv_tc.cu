@@ -99,6 +99,14 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
       sShift[c] = a.shift ? a.shift[c] : 0.f;
     }
   }
+  const bool full_groups = (a.Cg % 8) == 0;
+  // inputs of 2 or 4 channels: only the first bytes of group 0 are ever written, so the
+  // window is zeroed once here and the rest of it stays zero for every segment
+  const bool narrow = a.Cg == 2 || a.Cg == 4;
+  if (!full_groups) {
+    uint4* w4 = reinterpret_cast<uint4*>(sA);
+    for (int i = tid; i < nph * G * L; i += CONV_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -115,7 +123,6 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   bool ok = true;
   // window start (virtual output position) relative to the segment start
   const int wofs = (TAPS == 1) ? 0 : -(a.Po + 1);
-  const bool full_groups = (a.Cg % 8) == 0;
 
   for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x) {
     const int b = seg / a.segs_per_img;
@@ -125,9 +132,9 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
     // ---- stage the window: group fastest (coalesced global reads); plane (ph, g)
     //      holds L rows of 16 bytes ----
     for (int ph = 0; ph < nph; ++ph) {
-      const int total = G * L;
+      const int total = (narrow ? 1 : G) * L;
       for (int idx = tid; idx < total; idx += CONV_THREADS) {
-        const int g = idx % G, t = idx / G;
+        const int g = narrow ? 0 : idx % G, t = narrow ? idx : idx / G;
         const int q = qs + wofs + t;
         int iy = -1, ix = 0;
         if (TAPS == 1) {
@@ -148,7 +155,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
         uint8_t* dptr = sA + static_cast<size_t>((ph * G + g) * L + t) * 16;
         const bf16* px = xb + (static_cast<long>(iy < 0 ? 0 : iy) * a.Wi + ix) * a.Cg;
         if (full_groups) {
-          tc::cp_async16(smem_u32(dptr), iy >= 0 ? px + c0 : xb, iy >= 0 ? 16u : 0u);
+          const bool in = iy >= 0 && c0 < a.Cg;
+          tc::cp_async16(smem_u32(dptr), in ? px + c0 : xb, in ? 16u : 0u);
+        } else if (narrow) {
+          if (a.Cg == 2)
+            tc::cp_async_small<4>(smem_u32(dptr), iy >= 0 ? px : xb, iy >= 0 ? 4u : 0u);
+          else
+            tc::cp_async_small<8>(smem_u32(dptr), iy >= 0 ? px : xb, iy >= 0 ? 8u : 0u);
         } else {
           uint16_t tmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
           if (iy >= 0)
@@ -307,8 +320,9 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   using Cfg = ConvCfg<CS, COUT, TAPS>;
   ConvArgs a = a0;
   const int nph = a.mode == HELM_CONV_S2 ? 4 : 1;
-  // window budget: one CTA per SM for the heavy-weight layers, two otherwise
-  const size_t budget = Cfg::BBYTES > 40 * 1024 ? 200 * 1024 : 56 * 1024;
+  // window budget: one CTA per SM for the heavy-weight layers, two otherwise (register-
+  // limited to two anyway at 256 threads)
+  const size_t budget = Cfg::BBYTES > 40 * 1024 ? 200 * 1024 : 100 * 1024;
   const size_t fixed = Cfg::BBYTES + 2 * COUT * 4 + 64;
   const size_t plane_row = static_cast<size_t>(nph) * Cfg::G * 16;
   auto window_rows = [&](int segq) {

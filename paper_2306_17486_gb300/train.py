@@ -58,11 +58,14 @@ def smooth_plus_noise(B: int, N: int, gen: torch.Generator, ell: float = 4.0, no
 
 
 class Trainer:
-    """sizes: ((N_total, abl), ...) grids including the absorbing layer."""
+    """sizes: ((N_total, abl[, levels]), ...) grids including the absorbing layer, with
+    the V-cycle depth of the data generation (default `levels`); pattern: the size index
+    of each block of `block` steps, repeated (default: six small blocks for every four
+    large ones with two sizes, round robin otherwise)."""
 
     def __init__(self, net: Cnn, sizes=((128, 16), (256, 16)), batch: int = 32, lr: float = 1e-3,
                  steps: int = 2000, seed: int = 0, pool: int = 24, levels: int = 3, kappa_ell: float = 8.0,
-                 block: int = 100, kappas_per_batch: int = 4, device="cuda"):
+                 block: int = 100, kappas_per_batch: int = 4, pattern=None, device="cuda"):
         import synth
         self.net, self.batch, self.steps, self.block = net, batch, steps, block
         self.G = kappas_per_batch
@@ -72,13 +75,19 @@ class Trainer:
         self.gen.manual_seed(seed)
         self.rng = np.random.default_rng(seed)
         self.pools = []
-        for si, (N, abl) in enumerate(sizes):
+        if pattern is not None:
+            self.PATTERN = tuple(pattern)
+        elif len(sizes) > 2:
+            self.PATTERN = tuple(range(len(sizes)))
+        for si, size in enumerate(sizes):
+            N, abl = size[0], size[1]
+            lv = size[2] if len(size) > 2 else levels
             probs = []
             for j in range(pool):
                 kap = synth.grf_kappa(N - 2 * abl, abl, kappa_ell, seed=100000 * (si + 1) + j + 1000 * seed)
                 oh = 2 * np.pi / (10.0 * float(kap.max()))
                 probs.append(Problem(torch.tensor(kap, dtype=torch.float32, device=self.device), abl, oh,
-                                     gamma0=0.05, levels=levels))
+                                     gamma0=0.05, levels=lv))
             self.pools.append(probs)
         self.opt = Adam(net.params, lr=lr)
         self.step_i = 0
@@ -203,24 +212,36 @@ def main():
     ap = argparse.ArgumentParser(description="multiscale training of the encoder-solver network")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--sizes", default="128:16,256:32", help="N_total:absorbing-layer cells, comma separated")
+    ap.add_argument("--sizes", default="128:16,256:32",
+                    help="N_total:absorbing-layer cells[:V-cycle levels], comma separated")
+    ap.add_argument("--pattern", default=None, help="size index per block of 100 steps, comma separated")
     ap.add_argument("--skip-threshold", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--init", default=None, help="start from these weights (fine-tuning)")
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import synth
     net = Cnn(skip_threshold=a.skip_threshold)
-    net.load_dict(synth.random_params(init_spec(net), seed=a.seed))
-    sizes = tuple((int(t.split(":")[0]), int(t.split(":")[1])) for t in a.sizes.split(","))
-    tr = Trainer(net, sizes=sizes, batch=a.batch, steps=a.steps, seed=a.seed)
+    prev = {}
+    if a.init:
+        prev = load_weights(net, a.init)
+    else:
+        net.load_dict(synth.random_params(init_spec(net), seed=a.seed))
+    sizes = tuple(tuple(int(v) for v in t.split(":")) for t in a.sizes.split(","))
+    pattern = tuple(int(v) for v in a.pattern.split(",")) if a.pattern else None
+    tr = Trainer(net, sizes=sizes, batch=a.batch, steps=a.steps, seed=a.seed, lr=a.lr, pattern=pattern)
     t0 = time.time()
     hist = tr.run(a.steps)
     torch.cuda.synchronize()
     dt = time.time() - t0
-    save_weights(net, a.out, {"steps": a.steps, "batch": a.batch, "sizes": a.sizes, "seed": a.seed,
-                              "skip_threshold": a.skip_threshold, "seconds": dt,
-                              "history": [list(h) for h in hist]})
+    meta = {"steps": a.steps + int(prev.get("steps") or 0), "batch": a.batch, "sizes": a.sizes,
+            "pattern": a.pattern, "seed": a.seed, "lr": a.lr, "skip_threshold": a.skip_threshold,
+            "seconds": dt + float(prev.get("seconds") or 0.0), "history": [list(h) for h in hist]}
+    if a.init:
+        meta["init"] = {k: prev.get(k) for k in ("steps", "sizes", "seconds")}
+    save_weights(net, a.out, meta)
     print(f"trained {a.steps} steps in {dt:.1f} s -> {a.out}")
 
 
