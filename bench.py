@@ -266,7 +266,7 @@ def run_gpu(args, rank: int, world: int):
         dist.destroy_process_group()
 
 
-WEIGHTS = os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_128_256.npz")
+WEIGHTS = os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz")
 
 
 def _network(helm, dev, args):
@@ -281,7 +281,8 @@ def _network(helm, dev, args):
         return net, {"source": os.path.relpath(path, ROOT), "steps": meta.get("steps"),
                      "train_seconds": meta.get("seconds")}
     net.load_dict(synth.random_params(T.init_spec(net), seed=0))
-    tr = T.Trainer(net, sizes=((128, 16), (256, 32)), batch=32, steps=args.train_steps, seed=0)
+    tr = T.Trainer(net, sizes=((128, 16, 3), (256, 32, 3), (576, 32, 4)), batch=32, steps=args.train_steps, seed=0,
+                   pattern=(0, 2, 1, 2, 0, 2, 1, 2, 2, 2))
     t0 = time.time()
     tr.run(args.train_steps, log=None)
     torch.cuda.synchronize()

@@ -307,7 +307,7 @@ class Cnn:
         check(lib().helm_cnn_set_problem(self.handle, p.handle, None, 0, _stream()), "helm_cnn_set_problem")
 
     def apply(self, p: Problem, r: torch.Tensor, train: bool = False, ws: torch.Tensor | None = None):
-        """e = ||r|| Net(r / ||r||)."""
+        """e = s Net(r / s), s = RMS of r over the grid."""
         _need(r, torch.complex64, "r")
         B = r.shape[0]
         e = torch.empty_like(r)

@@ -7,11 +7,11 @@
 //   encoder (batch 1): (Re, Im) kappa^2(1 - gamma i) at I -> 3 downsampling modules
 //     [3x3 s2 conv, 3x3 conv, 3x3 conv, each + BN + softplus] -> enc1 (16, I/2),
 //     enc2 (32, I/4), enc3 (64, I/8)
-//   solver (batch B): x0 = R(r/||r||) -> level k: conv (s1, s2, s2) + BN + softplus
+//   solver (batch B): x0 = R(r/s), s = RMS(r), -> level k: conv (s1, s2, s2) + BN + softplus
 //     + enc_k, inverted bottleneck (1x1 expand + BN + softplus, dw 3x3 + BN + softplus,
-//     1x1 project + BN, + identity) -> g_k; level 4: 3 convs (first s2, or s1 when
-//     I < 512) -> implicit layer -> up modules (transposed conv + 2 convs, + g_{4-k})
-//     -> 1x1 projection 16 -> 2 + bias -> bilinear P to I -> times ||r||.
+//     1x1 project + BN, + identity) -> g_k; level 4: 3 convs (first s2, or s1 below the
+//     skip threshold) -> implicit layer -> up modules (transposed conv + 2 convs, + g_{4-k})
+//     -> 1x1 projection 16 -> 2 + bias -> bilinear P to I -> times s.
 #include <cmath>
 #include <cstring>
 
@@ -149,7 +149,7 @@ void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, 
 }
 
 void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
-                       int Bk) {
+                       int Bk, bool fuse_ib) {
   *pl = Plan();
   pl->I = I;
   pl->B = B;
@@ -171,11 +171,23 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
     if (k > 0) H /= 2;
     const std::string p = "s.l" + std::to_string(k + 1);
     const int f = pl->add_tensor(B, H, H, C[k]);
+    pl->layers.push_back(conv_layer(c, p + ".conv.w", p + ".bn", k == 0 ? HELM_CONV_S1 : HELM_CONV_S2, x, f, -1,
+                                    enc_ids[k]));
+    if (fuse_ib) {
+      g[k] = pl->add_tensor(B, H, H, C[k]);
+      Layer ib = conv_layer(c, p + ".ib.exp.w", p + ".ib.bn0", HELM_CONV_S1, f, g[k], -1, -1);
+      ib.kind = L_IB;
+      ib.wp_dw = c->pidx.at(p + ".ib.dw.w");
+      ib.bn_dw = c->bidx.at(p + ".ib.bn1");
+      ib.wp_proj = c->pidx.at(p + ".ib.proj.w");
+      ib.bn_proj = c->bidx.at(p + ".ib.bn2");
+      pl->layers.push_back(ib);
+      x = g[k];
+      continue;
+    }
     const int a = pl->add_tensor(B, H, H, t * C[k]);
     const int d = pl->add_tensor(B, H, H, t * C[k]);
     g[k] = pl->add_tensor(B, H, H, C[k]);
-    pl->layers.push_back(conv_layer(c, p + ".conv.w", p + ".bn", k == 0 ? HELM_CONV_S1 : HELM_CONV_S2, x, f, -1,
-                                    enc_ids[k]));
     pl->layers.push_back(conv_layer(c, p + ".ib.exp.w", p + ".ib.bn0", HELM_CONV_S1, f, a, -1, -1));
     Layer dw{};
     dw.kind = L_DW;
@@ -341,6 +353,22 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
       cl.add2_div = L.add2 >= 0 ? out.B / pl.t[L.add2].B : 1;
       cl.y = static_cast<__nv_bfloat16*>(ptr[L.out]);
       rc = conv_tc(cl, st);
+    } else if (L.kind == L_IB) {
+      IbLaunch il;
+      il.x = static_cast<const __nv_bfloat16*>(ptr[L.in]);
+      il.B = in.B;
+      il.H = in.H;
+      il.W = in.W;
+      il.C = in.C;
+      il.expansion = c->desc.expansion;
+      il.we = c->wpk + wpk_offset(c, L.wparam);
+      il.wp = c->wpk + wpk_offset(c, L.wp_proj);
+      il.wdw = c->params_dev + c->params[L.wp_dw].offset;
+      il.bn0 = fold;
+      il.bn1 = c->fold + c->bns[L.bn_dw].roff;
+      il.bn2 = c->fold + c->bns[L.bn_proj].roff;
+      il.y = static_cast<__nv_bfloat16*>(ptr[L.out]);
+      rc = ib_fused(il, st);
     } else if (L.kind == L_DW) {
       rc = launch_dw(static_cast<const __nv_bfloat16*>(ptr[L.in]), in.B, in.H, in.W, in.C,
                      c->params_dev + c->params[L.wparam].offset, fold, fold + C, L.act,
@@ -358,11 +386,11 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
 size_t cnn_forward_bytes(const helm_cnn* c, int I, int B) {
   Plan pl;
   int x0, u3, e[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, e, 1);
+  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, e, 1, true);
   return pl.arena + static_cast<size_t>(B) * 256 * sizeof(double) + 2 * 256 * B * sizeof(float) + 4096;
 }
 
-// e = ||r|| Net(r / ||r||) in inference mode, scratch from `cv`
+// e = s Net(r / s), s = RMS(r), in inference mode, scratch from `cv`
 int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float2* e, int B, Carve& cv,
                       cudaStream_t st) {
   if (c->enc_prob != p || c->enc_version != c->param_version) {
@@ -372,7 +400,7 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
   const int I = p->nx;
   Plan pl;
   int x0, u3, enc[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, enc, 1);
+  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, enc, 1, true);
   int rc = cnn_derive(c, pl.m, st);
   if (rc) return rc;
   char* arena = cv.take<char>(pl.arena);

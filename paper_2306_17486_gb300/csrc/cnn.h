@@ -26,6 +26,21 @@ struct ConvLaunch {
 };
 
 int conv_tc(const ConvLaunch& c, cudaStream_t st);
+
+// Evaluation-mode inverted bottleneck in one kernel (ib_fused.cu):
+// y = x + BN2(P softplus(BN1(dw(softplus(BN0(E x)))))), x, y BF16 NHWC [B][H][W][C].
+struct IbLaunch {
+  const __nv_bfloat16* x = nullptr;
+  int B = 0, H = 0, W = 0, C = 0, expansion = 6;
+  const __nv_bfloat16* we = nullptr;   // packed 1x1 expansion weights (conv packing, CS = C)
+  const __nv_bfloat16* wp = nullptr;   // packed 1x1 projection weights (CS = expansion C)
+  const float* wdw = nullptr;          // depthwise weights [expansion C][3][3], FP32
+  const float* bn0 = nullptr;          // folded BN (scale | shift) after each stage
+  const float* bn1 = nullptr;
+  const float* bn2 = nullptr;
+  __nv_bfloat16* y = nullptr;
+};
+int ib_fused(const IbLaunch& l, cudaStream_t st);
 int pack_conv_weights(const float* w, int Ci, int Co, int taps, int transposed, __nv_bfloat16* out, cudaStream_t st);
 
 }  // namespace helm

@@ -11,7 +11,7 @@
 
 namespace helm {
 
-enum LayerKind { L_CONV = 0, L_DW = 1, L_IMPL = 2 };
+enum LayerKind { L_CONV = 0, L_DW = 1, L_IMPL = 2, L_IB = 3 };
 
 struct ParamInfo {
   std::string name;
@@ -39,6 +39,9 @@ struct Layer {
   int mode, taps, ci, co, act;
   int in, out, add1, add2;  // tensor ids (-1: none); add2 may have batch 1 (broadcast)
   size_t wpk_off;    // element offset of this layer's packed weights
+  // L_IB (fused inverted bottleneck, inference only): wparam / bn = expansion,
+  // wp_dw / bn_dw = depthwise, wp_proj / bn_proj = projection
+  int wp_dw = -1, bn_dw = -1, wp_proj = -1, bn_proj = -1;
 };
 
 // A plan for one (I, B, skip) configuration: tensors and layers of either the encoder
@@ -91,8 +94,10 @@ namespace helm {
 // parameter and BN lookup
 inline int P(const helm_cnn* c, const std::string& n) { return c->pidx.at(n); }
 void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, int Bk);
+// fuse_ib: each inverted bottleneck as one L_IB layer (inference); otherwise expansion,
+// depthwise and projection as separate layers with their activations (training)
 void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
-                       int Bk);
+                       int Bk, bool fuse_ib = false);
 int cnn_derive(helm_cnn* c, int m, cudaStream_t st);  // pack weights, fold BN, build G_hat(m)
 int skip_for(const helm_cnn* c, int I);
 size_t packed_elems(const helm_cnn* c, const ParamInfo& pi);

@@ -26,12 +26,14 @@ __global__ void k_norm_partial(const float2* __restrict__ r, long n, int nblk, d
   const int b = blockIdx.y;
   const long chunk = (n + nblk - 1) / nblk;
   const long p0 = blockIdx.x * chunk, p1 = min(p0 + chunk, n);
-  double acc = 0.0;
+  // FP32 per thread (a few dozen terms; FP64 arithmetic is slow on this part), FP64
+  // across threads and blocks
+  float accf = 0.f;
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    float2 v = r[b * n + p];
-    acc += static_cast<double>(v.x) * v.x + static_cast<double>(v.y) * v.y;
+    const float2 v = r[b * n + p];
+    accf = fmaf(v.x, v.x, fmaf(v.y, v.y, accf));
   }
-  acc = warp_sum(acc);
+  double acc = warp_sum(static_cast<double>(accf));
   __shared__ double red[32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -256,20 +258,34 @@ __device__ __forceinline__ float2 load_pair<bf16>(const bf16* p, long idx, int C
 }
 
 // forward DFT of the zero-padded m x m block in `X` (m x m) into `F` (2m x 2m), using
-// scratch `R` (m x 2m); twiddle W[e] = exp(-2 pi i e / 2m)
+// scratch `R` (m x 2m); twiddle W[e] = exp(-2 pi i e / 2m).  The twiddle index u c mod 2m
+// is advanced incrementally (e += u, wrapped) instead of being recomputed per term.
+__device__ __forceinline__ int twiddle_step(int e, int d, int n) {
+  e += d;
+  return e >= n ? e - n : e;
+}
+
 __device__ void dft_pad_forward(const float2* X, float2* R, float2* F, const float2* Wt, int m) {
   const int n = 2 * m;
   for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
     const int r = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < m; ++c) acc = cadd(acc, cmul(X[r * m + c], Wt[(u * c) % n]));
+    int e = 0;
+    for (int c = 0; c < m; ++c) {
+      acc = cadd(acc, cmul(X[r * m + c], Wt[e]));
+      e = twiddle_step(e, u, n);
+    }
     R[i] = acc;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int v = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < m; ++r) acc = cadd(acc, cmul(R[r * n + u], Wt[(v * r) % n]));
+    int e = 0;
+    for (int r = 0; r < m; ++r) {
+      acc = cadd(acc, cmul(R[r * n + u], Wt[e]));
+      e = twiddle_step(e, v, n);
+    }
     F[i] = acc;
   }
   __syncthreads();
@@ -281,9 +297,11 @@ __device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const fl
   for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
     const int r = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
+    int e = 0;
     for (int v = 0; v < n; ++v) {
-      const float2 t = Wt[(v * r) % n];
+      const float2 t = Wt[e];
       acc = cadd(acc, cmul(F[v * n + u], make_float2(t.x, -t.y)));
+      e = twiddle_step(e, r, n);
     }
     R[i] = acc;
   }
@@ -292,9 +310,11 @@ __device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const fl
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
     const int r = i / m, c = i % m;
     float2 acc = make_float2(0.f, 0.f);
+    int e = 0;
     for (int u = 0; u < n; ++u) {
-      const float2 t = Wt[(u * c) % n];
+      const float2 t = Wt[e];
       acc = cadd(acc, cmul(R[r * n + u], make_float2(t.x, -t.y)));
+      e = twiddle_step(e, c, n);
     }
     Y[i] = cscale(acc, sc);
   }

@@ -452,14 +452,16 @@ __global__ void k_implicit_kgrad(const bf16* __restrict__ x, const float* __rest
   for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
     const int r = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < m; ++c) acc = cadd(acc, cmul(X[r * m + c], Wt[(u * c) % n]));
+    for (int c = 0, e = 0; c < m; ++c, e = (e + u >= n ? e + u - n : e + u))
+      acc = cadd(acc, cmul(X[r * m + c], Wt[e]));
     R[i] = acc;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int v = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < m; ++r) acc = cadd(acc, cmul(R[r * n + u], Wt[(v * r) % n]));
+    for (int r = 0, e = 0; r < m; ++r, e = (e + v >= n ? e + v - n : e + v))
+      acc = cadd(acc, cmul(R[r * n + u], Wt[e]));
     F1[i] = acc;
   }
   __syncthreads();
@@ -469,7 +471,8 @@ __global__ void k_implicit_kgrad(const bf16* __restrict__ x, const float* __rest
   for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
     const int r = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < m; ++c) acc = cadd(acc, cmul(X[r * m + c], Wt[(u * c) % n]));
+    for (int c = 0, e = 0; c < m; ++c, e = (e + u >= n ? e + u - n : e + u))
+      acc = cadd(acc, cmul(X[r * m + c], Wt[e]));
     R[i] = acc;
   }
   __syncthreads();
@@ -478,7 +481,8 @@ __global__ void k_implicit_kgrad(const bf16* __restrict__ x, const float* __rest
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int v = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < m; ++r) acc = cadd(acc, cmul(R[r * n + u], Wt[(v * r) % n]));
+    for (int r = 0, e = 0; r < m; ++r, e = (e + v >= n ? e + v - n : e + v))
+      acc = cadd(acc, cmul(R[r * n + u], Wt[e]));
     F2[i] = acc;
     out[i] = cscale(cmulc(F1[i], acc), sc);  // conj(X_hat) * F(pad gy) / n^2
   }

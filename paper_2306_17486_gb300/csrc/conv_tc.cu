@@ -14,8 +14,11 @@
 //   stride 1      : the input itself (output grid = input grid)
 //   stride 2      : four phase planes S_{py,px}(y,x) = in(2y+py, 2x+px); tap dy uses
 //                   phase (1, 0, 1)[dy+1] and shift (-1, 0, 0)[dy+1]
-//   transposed s2 : the zero-inserted upsampling up(2y, 2x) = in(y, x) at output
-//                   resolution, with the kernel flipped (dy -> 1 - ky)
+//   transposed s2 : sub-pixel form: the virtual grid is the INPUT grid, the window the
+//                   input itself, and each of the four output phases (oy mod 2,
+//                   ox mod 2) has its own accumulator and the 1, 2, 2 or 4 taps of the
+//                   flipped kernel that reach it (out(2y+py, 2x+px) sums in(y + a, x + c)
+//                   over a in {0, py}, c in {0, px}); no zero-inserted copy is staged
 //   1x1           : 128 consecutive pixels, Po = Wo
 // One thread issues all MMAs of a tile and commits them to an mbarrier; 8 warps read
 // the accumulator with tcgen05.ld (TMEM lane t = pixel q0 + t) and run the epilogue.
@@ -34,7 +37,8 @@ using bf16 = __nv_bfloat16;
 struct ConvArgs {
   const bf16* x;
   int B, Hi, Wi, Cg;     // input: batch, size, channels stored in global memory
-  int Ho, Wo, Po;        // output size, virtual pitch
+  int Ho, Wo, Po;        // virtual output grid (input grid for transposed s2), pitch
+  int Hout, Wout;        // stored output size (2 Ho x 2 Wo for transposed s2)
   int mode;
   const bf16* wpk;       // packed weights [taps][G][COUT][8]
   const float* scale;    // [COUT] or null (1)
@@ -48,17 +52,19 @@ struct ConvArgs {
   int seg_q;             // virtual output pixels per segment (whole rows for 3x3)
   int segs_per_img, nsegs;
   int L;                 // window rows per plane (odd)
+  int nwin;              // window buffers: 2 (next segment prefetched) or 1
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-template <int CS, int COUT, int TAPS>
+template <int CS, int COUT, int TAPS, int PH = 1>
 struct ConvCfg {
   static constexpr int G = CS / 8;                          // 16-byte groups per pixel
   static constexpr int NSPLIT = COUT > 256 ? 2 : 1;
   static constexpr int NH = COUT / NSPLIT;                  // N of one MMA
-  static constexpr int NBUF = 2 * COUT <= 512 ? 2 : 1;      // TMEM accumulators (double buffer)
-  static constexpr int NEED = NBUF * COUT;
+  static constexpr int ACC = PH * COUT;                     // accumulator columns per tile
+  static constexpr int NBUF = 2 * ACC <= 512 ? 2 : 1;       // TMEM accumulators (double buffer)
+  static constexpr int NEED = NBUF * ACC;
   static constexpr int NCOLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   static constexpr int BBYTES = TAPS * G * COUT * 16;
   static_assert(CS % 16 == 0, "K per tap must be a multiple of 16");
@@ -73,16 +79,17 @@ struct ConvCfg {
 // share TMEM lanes 32 (w mod 4) .. + 31 and split the output channels in 16-wide chunks.
 constexpr int CONV_THREADS = 256;
 
-template <int CS, int COUT, int TAPS>
+template <int CS, int COUT, int TAPS, int PH>
 __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
-  using Cfg = ConvCfg<CS, COUT, TAPS>;
+  using Cfg = ConvCfg<CS, COUT, TAPS, PH>;
   constexpr int G = Cfg::G;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
   uint8_t* sA = smem + Cfg::BBYTES;
   const int nph = (a.mode == HELM_CONV_S2) ? 4 : 1;
   const int L = a.L;
-  float* sScale = reinterpret_cast<float*>(sA + static_cast<size_t>(nph) * G * L * 16);
+  const size_t win_bytes = static_cast<size_t>(nph) * G * L * 16;   // one window buffer
+  float* sScale = reinterpret_cast<float*>(sA + a.nwin * win_bytes);
   float* sShift = sScale + COUT;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));   // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   const bool narrow = a.Cg == 2 || a.Cg == 4;
   if (!full_groups) {
     uint4* w4 = reinterpret_cast<uint4*>(sA);
-    for (int i = tid; i < nph * G * L; i += CONV_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < a.nwin * nph * G * L; i += CONV_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -117,18 +124,19 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+  const uint32_t sB_u = smem_u32(sB);
   constexpr uint32_t idesc = tc::idesc_bf16(128, Cfg::NH);
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
   // window start (virtual output position) relative to the segment start
-  const int wofs = (TAPS == 1) ? 0 : -(a.Po + 1);
+  const int wofs = (TAPS == 1 || PH == 4) ? 0 : -(a.Po + 1);
 
-  for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x) {
-    const int b = seg / a.segs_per_img;
-    const int qs = (seg % a.segs_per_img) * a.seg_q;
+  // stage segment `sg` into window buffer `win` with asynchronous copies (one commit
+  // group); the copies of the next segment are in flight while this one is computed
+  auto stage = [&](int sg, uint8_t* win) {
+    const int qs = (sg % a.segs_per_img) * a.seg_q;
     const int qe = min(qs + a.seg_q, a.Ho * a.Po);
-    const bf16* xb = a.x + static_cast<long>(b) * a.Hi * a.Wi * a.Cg;
+    const bf16* xb = a.x + static_cast<long>(sg / a.segs_per_img) * a.Hi * a.Wi * a.Cg;
     // ---- stage the window: group fastest (coalesced global reads); plane (ph, g)
     //      holds L rows of 16 bytes ----
     for (int ph = 0; ph < nph; ++ph) {
@@ -142,17 +150,15 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
         } else {
           const int yv = floordiv(q, a.Po), xv = q - yv * a.Po;
           if (yv >= 0 && yv < a.Ho && xv < a.Wo) {
-            if (a.mode == HELM_CONV_S1) {
+            if (a.mode == HELM_CONV_S1 || PH == 4) {
               iy = yv; ix = xv;
-            } else if (a.mode == HELM_CONV_S2) {
+            } else {   // stride 2: phase plane ph
               iy = 2 * yv + (ph >> 1); ix = 2 * xv + (ph & 1);
-            } else if (!(yv & 1) && !(xv & 1)) {  // transposed stride 2: zero-inserted upsampling
-              iy = yv >> 1; ix = xv >> 1;
             }
           }
         }
         const int c0 = 8 * g;
-        uint8_t* dptr = sA + static_cast<size_t>((ph * G + g) * L + t) * 16;
+        uint8_t* dptr = win + static_cast<size_t>((ph * G + g) * L + t) * 16;
         const bf16* px = xb + (static_cast<long>(iy < 0 ? 0 : iy) * a.Wi + ix) * a.Cg;
         if (full_groups) {
           const bool in = iy >= 0 && c0 < a.Cg;
@@ -171,7 +177,27 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
         }
       }
     }
-    tc::cp_async_wait_all();
+    tc::cp_async_commit();
+  };
+  const bool dbl = a.nwin == 2;
+  if (dbl && static_cast<int>(blockIdx.x) < a.nsegs) stage(blockIdx.x, sA);
+  int it = 0;
+  for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x, ++it) {
+    const int b = seg / a.segs_per_img;
+    const int qs = (seg % a.segs_per_img) * a.seg_q;
+    const int qe = min(qs + a.seg_q, a.Ho * a.Po);
+    uint8_t* cur = sA + (dbl ? (it & 1) * win_bytes : 0);
+    const uint32_t sA_u = smem_u32(cur);
+    if (dbl) {
+      if (seg + static_cast<int>(gridDim.x) < a.nsegs)
+        stage(seg + gridDim.x, sA + ((it + 1) & 1) * win_bytes);
+      else
+        tc::cp_async_commit();   // empty group keeps the count uniform
+      tc::cp_async_wait_group1();   // this segment's copies (all but the newest group) have landed
+    } else {
+      stage(seg, cur);
+      tc::cp_async_wait_all();
+    }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -180,6 +206,34 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
       tc::fence_after_sync();
       const int buf = j % Cfg::NBUF;
       const uint32_t lboA = static_cast<uint32_t>(L) * 16u;
+      if constexpr (PH == 4) {
+        // output phase ph = 2 py + px: taps (ty, tx) of the flipped kernel with ty in
+        // {1} (py = 0) or {0, 2} (py = 1), likewise tx; window offset (ty / 2) Po + tx / 2
+#pragma unroll 1
+        for (int ph = 0; ph < 4; ++ph) {
+          const int py = ph >> 1, px = ph & 1;
+          int kstep = 0;
+#pragma unroll 1
+          for (int a2 = 0; a2 <= py; ++a2) {
+#pragma unroll 1
+            for (int c2 = 0; c2 <= px; ++c2) {
+              const int ty = py ? 2 * a2 : 1, tx = px ? 2 * c2 : 1;
+              const int tap = ty * 3 + tx;
+              const int row = 128 * j + a2 * a.Po + c2;
+#pragma unroll
+              for (int kc = 0; kc < CS / 16; ++kc) {
+                const uint32_t aaddr = sA_u + static_cast<uint32_t>(((2 * kc) * L + row) * 16);
+                const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT) * 16);
+                tc::mma_bf16(tmem + buf * Cfg::ACC + ph * COUT, tc::sdesc(aaddr, lboA, 128),
+                             tc::sdesc(baddr, COUT * 16, 128), idesc, kstep > 0);
+                ++kstep;
+              }
+            }
+          }
+        }
+        tc::commit(&bar[buf]);
+        return;
+      }
       int kstep = 0;
 #pragma unroll 1
       for (int tap = 0; tap < TAPS; ++tap) {
@@ -203,7 +257,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
           for (int nh = 0; nh < Cfg::NSPLIT; ++nh) {
             const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT + nh * Cfg::NH) * 16);
             const uint64_t bd = tc::sdesc(baddr, COUT * 16, 128);
-            tc::mma_bf16(tmem + buf * COUT + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
+            tc::mma_bf16(tmem + buf * Cfg::ACC + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
           }
           ++kstep;
         }
@@ -224,51 +278,55 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
       const int q = qs + 128 * j + (tid & 127);
       const int y = q / a.Po, x = q - y * a.Po;
       const bool valid = ok && q < qe && x < a.Wo;
-      const long pix = (static_cast<long>(b) * a.Ho + y) * a.Wo + x;
-      const long pix2 = (static_cast<long>(b / a.add2_div) * a.Ho + y) * a.Wo + x;
 #pragma unroll 1
-      for (int c0 = 16 * chalf; c0 < COUT; c0 += 32) {
-        float v[16];
-        tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * COUT + c0, v);
-        if (!valid) continue;
-        if (a.yraw) {
-          float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
+      for (int ph = 0; ph < PH; ++ph) {
+        const int oy = PH == 4 ? 2 * y + (ph >> 1) : y, ox = PH == 4 ? 2 * x + (ph & 1) : x;
+        const long pix = (static_cast<long>(b) * a.Hout + oy) * a.Wout + ox;
+        const long pix2 = (static_cast<long>(b / a.add2_div) * a.Hout + oy) * a.Wout + ox;
+#pragma unroll 1
+        for (int c0 = 16 * chalf; c0 < COUT; c0 += 32) {
+          float v[16];
+          tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * Cfg::ACC + ph * COUT + c0, v);
+          if (!valid) continue;
+          if (a.yraw) {
+            float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-        }
-        if (a.y) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
-            v[i] = a.act ? tc::softplus_fast(t) : t;
+            for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
           }
-          if (a.add1) {
-            const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
+          if (a.y) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              uint4 u = pp[h];
-              const bf16* e = reinterpret_cast<const bf16*>(&u);
-#pragma unroll
-              for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+            for (int i = 0; i < 16; ++i) {
+              float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
+              v[i] = a.act ? tc::softplus_fast(t) : t;
             }
-          }
-          if (a.add2) {
-            const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
+            if (a.add1) {
+              const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              uint4 u = pp[h];
-              const bf16* e = reinterpret_cast<const bf16*>(&u);
+              for (int h = 0; h < 2; ++h) {
+                uint4 u = pp[h];
+                const bf16* e = reinterpret_cast<const bf16*>(&u);
 #pragma unroll
-              for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+                for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+              }
             }
-          }
-          uint4 o[2];
-          __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+            if (a.add2) {
+              const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-          uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
-          dst[0] = o[0];
-          dst[1] = o[1];
+              for (int h = 0; h < 2; ++h) {
+                uint4 u = pp[h];
+                const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+              }
+            }
+            uint4 o[2];
+            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
+            dst[0] = o[0];
+            dst[1] = o[1];
+          }
         }
       }
       tc::fence_before_sync();
@@ -279,8 +337,9 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
       }
       if (!ok) break;
     }
-    __syncthreads();  // the window is re-staged by the next segment
+    __syncthreads();  // this window buffer is re-staged two segments later
   }
+  tc::cp_async_wait_all();   // no copy may still target shared memory at exit
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, Cfg::NCOLS);
 }
@@ -315,9 +374,9 @@ __global__ void k_pack_weights(const float* __restrict__ w, int Ci, int Co, int 
   }
 }
 
-template <int CS, int COUT, int TAPS>
+template <int CS, int COUT, int TAPS, int PH = 1>
 int launch_t(const ConvArgs& a0, cudaStream_t st) {
-  using Cfg = ConvCfg<CS, COUT, TAPS>;
+  using Cfg = ConvCfg<CS, COUT, TAPS, PH>;
   ConvArgs a = a0;
   const int nph = a.mode == HELM_CONV_S2 ? 4 : 1;
   // window budget: one CTA per SM for the heavy-weight layers, two otherwise (register-
@@ -327,23 +386,36 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   const size_t plane_row = static_cast<size_t>(nph) * Cfg::G * 16;
   auto window_rows = [&](int segq) {
     const int nt = (segq + 127) / 128;
-    int Lr = 128 * nt + (TAPS == 1 ? 0 : (a.mode == HELM_CONV_S2 ? a.Po + 1 : 2 * a.Po + 2));
+    int Lr = 128 * nt + (TAPS == 1 ? 0 : (a.mode == HELM_CONV_S2 || PH == 4 ? a.Po + 2 : 2 * a.Po + 2));
     return Lr | 1;
   };
-  if (TAPS == 1) {
-    int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (plane_row * 128));
-    tiles = std::max(1, std::min(tiles, 16));
-    a.seg_q = 128 * tiles;
-  } else {
-    int R = 1;
-    for (int r = 2; r <= std::min(a.Ho, 32); ++r)
-      if (fixed + plane_row * window_rows(r * a.Po) <= budget) R = r;
-    a.seg_q = R * a.Po;
-  }
-  a.L = window_rows(a.seg_q);
+  // window sizing for `nw` buffers; two (the next segment prefetched) when they fit
+  auto size_for = [&](int nw) {
+    if (TAPS == 1) {
+      int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (nw * plane_row * 128));
+      tiles = std::max(1, std::min(tiles, 16));
+      a.seg_q = 128 * tiles;
+    } else {
+      int R = 1;
+      for (int r = 2; r <= std::min(a.Ho, 32); ++r)
+        if (fixed + nw * plane_row * window_rows(r * a.Po) <= budget) R = r;
+      a.seg_q = R * a.Po;
+    }
+    a.L = window_rows(a.seg_q);
+    a.nwin = nw;
+    return fixed + nw * plane_row * a.L;
+  };
+  // two buffers only where they cost no segment length (a shorter segment re-reads more
+  // halo rows, which measured slower than the lost overlap)
+  size_t smem = size_for(1);
+  const int q1 = a.seg_q;
+  const size_t smem2 = size_for(2);
+  if (a.seg_q == q1 && smem2 <= 227 * 1024)
+    smem = smem2;
+  else
+    smem = size_for(1);
   a.segs_per_img = helm::div_up(static_cast<long>(a.Ho) * a.Po, a.seg_q);
   a.nsegs = a.segs_per_img * a.B;
-  const size_t smem = fixed + plane_row * a.L;
   if (smem > 227 * 1024) {
     helm::set_error("conv: shared memory %zu bytes exceeds the per-CTA limit (grid row too wide)", smem);
     return HELM_ESHAPE;
@@ -351,18 +423,19 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   static int nsm = 0;
   static bool attr = false;
   if (!attr) {
-    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    227 * 1024));
     int dev;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     attr = true;
   }
-  int per_sm = 0;
-  HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CS, COUT, TAPS>, CONV_THREADS, smem));
-  per_sm = std::max(1, std::min(per_sm, 512 / Cfg::NCOLS));
+  // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA), TMEM
+  // columns (512 per SM) and registers (at most two 256-thread CTAs below 128 registers)
+  int per_sm = static_cast<int>((228 * 1024) / (smem + 1024));
+  per_sm = std::max(1, std::min({per_sm, 512 / Cfg::NCOLS, 2}));
   const int grid = std::max(1, std::min(a.nsegs, nsm * per_sm));
-  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS><<<grid, CONV_THREADS, smem, st>>>(a));
+  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS, PH><<<grid, CONV_THREADS, smem, st>>>(a));
   HELM_CHECK_LAUNCH("k_conv_tc");
   return HELM_OK;
 }
@@ -412,15 +485,29 @@ int conv_tc(const ConvLaunch& c, cudaStream_t st) {
     a.Wo = c.Wi / 2;
     a.Po = a.Wo + 1;
   } else if (c.mode == HELM_CONV_T2) {
-    a.Ho = 2 * c.Hi;
-    a.Wo = 2 * c.Wi;
+    a.Ho = c.Hi;   // virtual grid = input grid (sub-pixel form)
+    a.Wo = c.Wi;
     a.Po = a.Wo + 1;
   } else {
     a.Ho = c.Hi;
     a.Wo = c.Wi;
     a.Po = a.Wo + 1;
   }
+  a.Hout = c.mode == HELM_CONV_T2 ? 2 * a.Ho : a.Ho;
+  a.Wout = c.mode == HELM_CONV_T2 ? 2 * a.Wo : a.Wo;
   const int CS = conv_cs(c.Ci);
+  if (c.mode == HELM_CONV_T2 && taps == 9) {
+#define HELM_CONV_T2_CASE(cs, co) \
+  if (CS == cs && c.Co == co) return launch_t<cs, co, 9, 4>(a, st);
+    HELM_CONV_T2_CASE(16, 16)
+    HELM_CONV_T2_CASE(32, 16)
+    HELM_CONV_T2_CASE(32, 32)
+    HELM_CONV_T2_CASE(64, 32)
+    HELM_CONV_T2_CASE(64, 64)
+#undef HELM_CONV_T2_CASE
+    set_error("conv: no transposed tensor-core kernel for Cin=%d Cout=%d", c.Ci, c.Co);
+    return HELM_EINVAL;
+  }
 #define HELM_CONV_CASE(cs, co, tp) \
   if (CS == cs && c.Co == co && taps == tp) return launch_t<cs, co, tp>(a, st);
   HELM_CONV_CASE(16, 16, 9)

@@ -9,7 +9,7 @@ Every step: `kappas_per_batch` slowness models from a seeded pool of the step's 
 its own kappa, so BatchNorm statistics average over models), a batch of random smooth-plus-noise
 vectors x (inputs: drawn with a seeded torch generator on the device), per-sample
 iteration counts k ~ U{2..20}, then on the library's kernels:
-    (e, r) = Eq. (17) pairs, normalised by ||r||      helm_datagen_pairs
+    (e, r) = Eq. (17) pairs, normalised by RMS(r)     helm_datagen_pairs
     e_pred = Net(r) with batch-statistics BN          helm_cnn_apply(train=1)
     loss, dL/de = Eq. (16)                            helm_mse_loss
     dL/dtheta                                         helm_cnn_precond_backward
