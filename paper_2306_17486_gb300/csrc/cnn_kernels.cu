@@ -322,7 +322,7 @@ __device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const fl
 }
 
 template <typename TIn, typename TOut>
-__global__ void k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat, int conj_g,
+__global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat, int conj_g,
                            TOut* __restrict__ y, int accumulate) {
   const int b = blockIdx.y, k = blockIdx.x;
   const int n = 2 * m;
@@ -464,12 +464,17 @@ __global__ void k_greens(const float* __restrict__ Kpar, int nk, int m, float ep
 }
 
 // ---- projection 1x1 (C -> 2, + bias) at I/2, bilinear prolongation to I, times s ----
-// one thread per pair of fine columns (2X, 2X+1) of a fine row: the projections of the
-// (at most) two coarse rows x three coarse columns it needs are computed once
+// one CTA per (sample b, coarse row J): the 1x1 projections of coarse rows J and J + 1
+// are computed once into shared memory, then the CTA writes fine rows 2J and 2J + 1
+// (bilinear P: even fine index = coarse value, odd = mean of the two neighbours, zero
+// beyond the last coarse row / column)
 constexpr int PJ_C = 16;
+constexpr int PJ_MAXNC = 2048;
 __global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u, int B, int Nc, int C,
                                                       const float* __restrict__ w, const float* __restrict__ bias,
                                                       const float* __restrict__ s, float2* __restrict__ e) {
+  __shared__ float2 Pk[2][PJ_MAXNC + 1];
+  const int J = blockIdx.x, b = blockIdx.y;
   float w0[PJ_C], w1[PJ_C];
 #pragma unroll
   for (int ch = 0; ch < PJ_C; ++ch) {
@@ -477,44 +482,37 @@ __global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u
     w1[ch] = w[C + ch];
   }
   const float b0 = bias[0], b1 = bias[1];
-  const int N = 2 * Nc;
-  const long total = static_cast<long>(B) * N * Nc;   // (b, Y, K): fine pixels (Y, 2K) and (Y, 2K+1)
-  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long>(gridDim.x) * blockDim.x) {
-    const int b = static_cast<int>(i / (static_cast<long>(N) * Nc));
-    const int Y = static_cast<int>((i / Nc) % N), K = static_cast<int>(i % Nc);
-    const int J = Y >> 1;
-    const float wy = (Y & 1) ? 0.5f : 1.f;
-    float2 pk[2][2];  // [row a][col c]: projection at coarse (J + a, K + c)
+  for (int i = threadIdx.x; i < 2 * (Nc + 1); i += blockDim.x) {
+    const int a = i / (Nc + 1), K = i - a * (Nc + 1);
+    float2 pv = make_float2(0.f, 0.f);
+    if (J + a < Nc && K < Nc) {
+      const uint4* up = reinterpret_cast<const uint4*>(u + ((static_cast<long>(b) * Nc + J + a) * Nc + K) * C);
+      float p0 = b0, p1 = b1;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int h = 0; h < PJ_C / 8; ++h) {
+        const uint4 v = up[h];
+        const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        pk[a][c] = make_float2(0.f, 0.f);
-        const int JJ = J + a, KK = K + c;
-        if ((a == 1 && !(Y & 1)) || JJ >= Nc || KK >= Nc) continue;
-        const uint4* up = reinterpret_cast<const uint4*>(u + ((static_cast<long>(b) * Nc + JJ) * Nc + KK) * C);
-        float p0 = b0, p1 = b1;
-#pragma unroll
-        for (int h = 0; h < PJ_C / 8; ++h) {
-          uint4 v = up[h];
-          const bf16* e8 = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float f = __bfloat162float(e8[q]);
-            p0 = fmaf(w0[8 * h + q], f, p0);
-            p1 = fmaf(w1[8 * h + q], f, p1);
-          }
+        for (int q = 0; q < 4; ++q) {
+          const float2 f = __bfloat1622float2(e2[q]);
+          p0 = fmaf(w0[8 * h + 2 * q], f.x, fmaf(w0[8 * h + 2 * q + 1], f.y, p0));
+          p1 = fmaf(w1[8 * h + 2 * q], f.x, fmaf(w1[8 * h + 2 * q + 1], f.y, p1));
         }
-        pk[a][c] = make_float2(p0, p1);
       }
-    // rows: even Y -> row J; odd Y -> (J + J+1)/2
-    const float2 r0 = (Y & 1) ? cscale(cadd(pk[0][0], pk[1][0]), wy) : pk[0][0];
-    const float2 r1 = (Y & 1) ? cscale(cadd(pk[0][1], pk[1][1]), wy) : pk[0][1];
-    const float sc = s[b];
-    float2* eo = e + (static_cast<long>(b) * N + Y) * N + 2 * K;
+      pv = make_float2(p0, p1);
+    }
+    Pk[a][K] = pv;
+  }
+  __syncthreads();
+  const int N = 2 * Nc;
+  const float sc = s[b];
+  for (int i = threadIdx.x; i < 2 * Nc; i += blockDim.x) {
+    const int af = i / Nc, K = i - af * Nc;   // fine row 2J + af, fine columns 2K, 2K + 1
+    const float2 r0 = af ? cscale(cadd(Pk[0][K], Pk[1][K]), 0.5f) : Pk[0][K];
+    const float2 r1 = af ? cscale(cadd(Pk[0][K + 1], Pk[1][K + 1]), 0.5f) : Pk[0][K + 1];
     const float2 ev = cscale(r0, sc);
     const float2 od = cscale(cscale(cadd(r0, r1), 0.5f), sc);
+    float2* eo = e + (static_cast<long>(b) * N + 2 * J + af) * N + 2 * K;
     *reinterpret_cast<float4*>(eo) = make_float4(ev.x, ev.y, od.x, od.y);
   }
 }
@@ -614,8 +612,11 @@ int launch_proj(const bf16* u, int B, int Nc, int C, const float* w, const float
     set_error("projection: kernel built for %d input channels", PJ_C);
     return HELM_EINVAL;
   }
-  const long total = static_cast<long>(B) * 2 * Nc * Nc;
-  HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<grid_for(total), 256, 0, st>>>(u, B, Nc, C, w, bias, s, e));
+  if (Nc > PJ_MAXNC || B > 65535) {
+    set_error("projection: coarse size %d or batch %d beyond the kernel's limits (%d, 65535)", Nc, B, PJ_MAXNC);
+    return HELM_ESHAPE;
+  }
+  HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<dim3(Nc, B), 256, 0, st>>>(u, B, Nc, C, w, bias, s, e));
   HELM_CHECK_LAUNCH("k_proj_prolong");
   return HELM_OK;
 }

@@ -57,44 +57,58 @@ struct ConvArgs {
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-template <int CS, int COUT, int TAPS, int PH = 1>
+template <int CS, int COUT, int TAPS, int PH = 1, int MTR = 2>
 struct ConvCfg {
   static constexpr int G = CS / 8;                          // 16-byte groups per pixel
   static constexpr int NSPLIT = COUT > 256 ? 2 : 1;
   static constexpr int NH = COUT / NSPLIT;                  // N of one MMA
-  static constexpr int ACC = PH * COUT;                     // accumulator columns per tile
-  static constexpr int NBUF = 2 * ACC <= 512 ? 2 : 1;       // TMEM accumulators (double buffer)
-  static constexpr int NEED = NBUF * ACC;
-  static constexpr int NCOLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
+  static constexpr int ACC = PH * COUT;                     // accumulator columns per M-tile
   static constexpr int BBYTES = TAPS * G * COUT * 16;
+  // M-tiles per step: two (256 pixels, one per epilogue warpgroup) while the two
+  // double-buffered steps fit in 256 TMEM columns (two CTAs per SM), for light-weight
+  // layers whose two-tile window fits beside the weights; MTR = 1 forces one
+  static constexpr int MT =
+      (MTR == 2 && 4 * ACC <= 256 && BBYTES <= 40 * 1024 && (TAPS == 9 || CS <= 192)) ? 2 : 1;
+  static constexpr int STEP = MT * ACC;                     // accumulator columns per step
+  static constexpr int NBUF = 2 * STEP <= 512 ? 2 : 1;      // TMEM accumulators (double buffer)
+  static constexpr int NEED = NBUF * STEP;
+  static constexpr int NCOLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   static_assert(CS % 16 == 0, "K per tap must be a multiple of 16");
   static_assert(NH % 16 == 0 && NH <= 256, "N per MMA");
 };
 
-// One CTA (8 warps) works through segments (a band of whole output rows of one image,
-// or for 1x1 a run of pixels): it stages the segment's input window once with
-// asynchronous 16-byte copies (zero-filled outside the image), then for every
-// 128-pixel M-tile one thread issues the MMAs into one of two TMEM accumulators while
-// the warps run the epilogue of the previous tile from the other.  Warps w and w + 4
-// share TMEM lanes 32 (w mod 4) .. + 31 and split the output channels in 16-wide chunks.
-constexpr int CONV_THREADS = 256;
+// One CTA works through segments (a band of whole output rows of one image, or for 1x1
+// a run of pixels): all warps stage the segment's input window with asynchronous
+// 16-byte copies (zero-filled outside the image); then warp 8 alone issues the MMAs of
+// every step (one or two 128-pixel M-tiles) into one of two TMEM accumulators, and
+// warps 0-7 run the epilogues.  The hand-off is two mbarrier pairs: `full` (MMA
+// commit -> epilogue) and `empty` (the 8 epilogue warps -> MMA warp), so steps flow
+// without block-wide barriers; the block synchronises only between segments, when the
+// window is restaged.  Epilogue warps w and w + 4 share TMEM lanes 32 (w mod 4) .. + 31:
+// with two M-tiles per step warpgroup g takes tile g and all channels, with one the two
+// warpgroups split the channels in 16-wide chunks.
+constexpr int CONV_EPI_WARPS = 8;
+constexpr int CONV_THREADS = 32 * (CONV_EPI_WARPS + 1);
 
-template <int CS, int COUT, int TAPS, int PH>
+template <int CS, int COUT, int TAPS, int PH, int MTR>
 __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
-  using Cfg = ConvCfg<CS, COUT, TAPS, PH>;
+  using Cfg = ConvCfg<CS, COUT, TAPS, PH, MTR>;
   constexpr int G = Cfg::G;
+  constexpr int MT = Cfg::MT;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
   uint8_t* sA = smem + Cfg::BBYTES;
   const int nph = (a.mode == HELM_CONV_S2) ? 4 : 1;
   const int L = a.L;
-  const size_t win_bytes = static_cast<size_t>(nph) * G * L * 16;   // one window buffer
-  float* sScale = reinterpret_cast<float*>(sA + a.nwin * win_bytes);
+  const size_t win_bytes = static_cast<size_t>(nph) * G * L * 16;
+  float* sScale = reinterpret_cast<float*>(sA + win_bytes);
   float* sShift = sScale + COUT;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));   // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int lane_q = warp & 3, chalf = warp >> 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sShift + COUT + (COUT & 1));   // [2]
+  uint64_t* empty = full + 2;                                                // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == CONV_EPI_WARPS;
+  const int lane_q = warp & 3, chalf = (warp >> 2) & 1;
 
   if (warp == 0) tc::tmem_alloc(tslot, Cfg::NCOLS);
   {
@@ -112,11 +126,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   const bool narrow = a.Cg == 2 || a.Cg == 4;
   if (!full_groups) {
     uint4* w4 = reinterpret_cast<uint4*>(sA);
-    for (int i = tid; i < a.nwin * nph * G * L; i += CONV_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < nph * G * L; i += CONV_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], CONV_EPI_WARPS);
+    mbar_init(&empty[1], CONV_EPI_WARPS);
     fence_mbar_init();
   }
   tc::fence_proxy_async();
@@ -124,19 +140,34 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t sB_u = smem_u32(sB);
+  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   constexpr uint32_t idesc = tc::idesc_bf16(128, Cfg::NH);
-  uint32_t phase[2] = {0u, 0u};
+  // descriptor bits other than the start address (the address field is OR-ed in)
+  const uint64_t dA = tc::sdesc(0, static_cast<uint32_t>(L) * 16u, 128);
+  const uint64_t dB = tc::sdesc(0, COUT * 16, 128);
+  // window offset (rows) and phase plane of each tap, for the MMA warp
+  int toff[9], tpl[9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ty = tap / 3, tx = tap % 3;
+    if (a.mode == HELM_CONV_S2) {
+      toff[tap] = (ty == 0 ? 0 : 1) * a.Po + (tx == 0 ? 0 : 1);
+      tpl[tap] = (ty == 1 ? 0 : 2) + (tx == 1 ? 0 : 1);
+    } else {
+      toff[tap] = ty * a.Po + tx;
+      tpl[tap] = 0;
+    }
+  }
   bool ok = true;
+  uint32_t gstep = 0;   // steps of this CTA over all its segments (buffer and phase index)
   // window start (virtual output position) relative to the segment start
   const int wofs = (TAPS == 1 || PH == 4) ? 0 : -(a.Po + 1);
 
-  // stage segment `sg` into window buffer `win` with asynchronous copies (one commit
-  // group); the copies of the next segment are in flight while this one is computed
-  auto stage = [&](int sg, uint8_t* win) {
-    const int qs = (sg % a.segs_per_img) * a.seg_q;
+  for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x) {
+    const int b = seg / a.segs_per_img;
+    const int qs = (seg % a.segs_per_img) * a.seg_q;
     const int qe = min(qs + a.seg_q, a.Ho * a.Po);
-    const bf16* xb = a.x + static_cast<long>(sg / a.segs_per_img) * a.Hi * a.Wi * a.Cg;
+    const bf16* xb = a.x + static_cast<long>(b) * a.Hi * a.Wi * a.Cg;
     // ---- stage the window: group fastest (coalesced global reads); plane (ph, g)
     //      holds L rows of 16 bytes ----
     for (int ph = 0; ph < nph; ++ph) {
@@ -158,7 +189,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
           }
         }
         const int c0 = 8 * g;
-        uint8_t* dptr = win + static_cast<size_t>((ph * G + g) * L + t) * 16;
+        uint8_t* dptr = sA + static_cast<size_t>((ph * G + g) * L + t) * 16;
         const bf16* px = xb + (static_cast<long>(iy < 0 ? 0 : iy) * a.Wi + ix) * a.Cg;
         if (full_groups) {
           const bool in = iy >= 0 && c0 < a.Cg;
@@ -177,169 +208,142 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
         }
       }
     }
-    tc::cp_async_commit();
-  };
-  const bool dbl = a.nwin == 2;
-  if (dbl && static_cast<int>(blockIdx.x) < a.nsegs) stage(blockIdx.x, sA);
-  int it = 0;
-  for (int seg = blockIdx.x; seg < a.nsegs && ok; seg += gridDim.x, ++it) {
-    const int b = seg / a.segs_per_img;
-    const int qs = (seg % a.segs_per_img) * a.seg_q;
-    const int qe = min(qs + a.seg_q, a.Ho * a.Po);
-    uint8_t* cur = sA + (dbl ? (it & 1) * win_bytes : 0);
-    const uint32_t sA_u = smem_u32(cur);
-    if (dbl) {
-      if (seg + static_cast<int>(gridDim.x) < a.nsegs)
-        stage(seg + gridDim.x, sA + ((it + 1) & 1) * win_bytes);
-      else
-        tc::cp_async_commit();   // empty group keeps the count uniform
-      tc::cp_async_wait_group1();   // this segment's copies (all but the newest group) have landed
-    } else {
-      stage(seg, cur);
-      tc::cp_async_wait_all();
-    }
+    tc::cp_async_wait_all();
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
-    const int ntiles = (qe - qs + 127) / 128;
-    auto issue = [&](int j) {
-      tc::fence_after_sync();
-      const int buf = j % Cfg::NBUF;
-      const uint32_t lboA = static_cast<uint32_t>(L) * 16u;
-      if constexpr (PH == 4) {
-        // output phase ph = 2 py + px: taps (ty, tx) of the flipped kernel with ty in
-        // {1} (py = 0) or {0, 2} (py = 1), likewise tx; window offset (ty / 2) Po + tx / 2
-#pragma unroll 1
-        for (int ph = 0; ph < 4; ++ph) {
-          const int py = ph >> 1, px = ph & 1;
-          int kstep = 0;
-#pragma unroll 1
-          for (int a2 = 0; a2 <= py; ++a2) {
-#pragma unroll 1
-            for (int c2 = 0; c2 <= px; ++c2) {
-              const int ty = py ? 2 * a2 : 1, tx = px ? 2 * c2 : 1;
-              const int tap = ty * 3 + tx;
-              const int row = 128 * j + a2 * a.Po + c2;
+    tc::fence_after_sync();
+    const int nsteps = (qe - qs + 128 * MT - 1) / (128 * MT);
+
+    if (mma_warp) {
+      // ---- MMA issue: one thread, all steps of the segment ----
+      if (lane == 0) {
+        for (int j = 0; j < nsteps; ++j) {
+          const uint32_t g = gstep + j, buf = g % Cfg::NBUF, use = g / Cfg::NBUF;
+          if (use > 0) ok = mbar_wait_bounded(&empty[buf], (use - 1) & 1u, HELM_DEVERR_MMA_WAIT) && ok;
+          tc::fence_after_sync();
 #pragma unroll
-              for (int kc = 0; kc < CS / 16; ++kc) {
-                const uint32_t aaddr = sA_u + static_cast<uint32_t>(((2 * kc) * L + row) * 16);
-                const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT) * 16);
-                tc::mma_bf16(tmem + buf * Cfg::ACC + ph * COUT, tc::sdesc(aaddr, lboA, 128),
-                             tc::sdesc(baddr, COUT * 16, 128), idesc, kstep > 0);
-                ++kstep;
+          for (int mt = 0; mt < MT; ++mt) {
+            const int row0 = 128 * (MT * j + mt);
+            const uint32_t dcol = buf * Cfg::STEP + mt * Cfg::ACC;
+            if constexpr (PH == 4) {
+              // output phase ph = 2 py + px: taps (ty, tx) of the flipped kernel with ty
+              // in {1} (py = 0) or {0, 2} (py = 1), likewise tx; window offset
+              // (ty / 2) Po + tx / 2
+#pragma unroll
+              for (int ph = 0; ph < 4; ++ph) {
+                const int py = ph >> 1, px = ph & 1;
+                int kstep = 0;
+#pragma unroll
+                for (int a2 = 0; a2 <= py; ++a2)
+#pragma unroll
+                  for (int c2 = 0; c2 <= px; ++c2) {
+                    const int tap = (py ? 2 * a2 : 1) * 3 + (px ? 2 * c2 : 1);
+                    const int row = row0 + a2 * a.Po + c2;
+#pragma unroll
+                    for (int kc = 0; kc < CS / 16; ++kc) {
+                      const uint32_t aaddr = sA_u + static_cast<uint32_t>(((2 * kc) * L + row) * 16);
+                      const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT) * 16);
+                      tc::mma_bf16(tmem + dcol + ph * COUT, dA | (aaddr >> 4), dB | (baddr >> 4), idesc, kstep > 0);
+                      ++kstep;
+                    }
+                  }
+              }
+            } else {
+#pragma unroll
+              for (int tap = 0; tap < TAPS; ++tap) {
+                const int row = row0 + (TAPS == 9 ? toff[tap] : 0);
+                const int pl = TAPS == 9 ? tpl[tap] : 0;
+#pragma unroll
+                for (int kc = 0; kc < CS / 16; ++kc) {
+                  const uint32_t aaddr = sA_u + static_cast<uint32_t>(((pl * G + 2 * kc) * L + row) * 16);
+#pragma unroll
+                  for (int nh = 0; nh < Cfg::NSPLIT; ++nh) {
+                    const uint32_t baddr =
+                        sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT + nh * Cfg::NH) * 16);
+                    tc::mma_bf16(tmem + dcol + nh * Cfg::NH, dA | (aaddr >> 4), dB | (baddr >> 4), idesc,
+                                 tap > 0 || kc > 0);
+                  }
+                }
               }
             }
           }
-        }
-        tc::commit(&bar[buf]);
-        return;
-      }
-      int kstep = 0;
-#pragma unroll 1
-      for (int tap = 0; tap < TAPS; ++tap) {
-        int row = 128 * j, ph = 0;
-        if (TAPS == 9) {
-          const int ty = tap / 3, tx = tap % 3;
-          if (a.mode == HELM_CONV_S2) {
-            const int sy = ty == 0 ? -1 : 0, py = ty == 1 ? 0 : 1;
-            const int sx = tx == 0 ? -1 : 0, px = tx == 1 ? 0 : 1;
-            ph = py * 2 + px;
-            row += (sy + 1) * a.Po + (sx + 1);
-          } else {
-            row += ty * a.Po + tx;
-          }
-        }
-#pragma unroll
-        for (int kc = 0; kc < CS / 16; ++kc) {
-          const uint32_t aaddr = sA_u + static_cast<uint32_t>(((ph * G + 2 * kc) * L + row) * 16);
-          const uint64_t ad = tc::sdesc(aaddr, lboA, 128);
-#pragma unroll
-          for (int nh = 0; nh < Cfg::NSPLIT; ++nh) {
-            const uint32_t baddr = sB_u + static_cast<uint32_t>(((tap * G + 2 * kc) * COUT + nh * Cfg::NH) * 16);
-            const uint64_t bd = tc::sdesc(baddr, COUT * 16, 128);
-            tc::mma_bf16(tmem + buf * Cfg::ACC + nh * Cfg::NH, ad, bd, idesc, kstep > 0);
-          }
-          ++kstep;
+          tc::commit(&full[buf]);
         }
       }
-      tc::commit(&bar[buf]);
-    };
-    if (tid == 0) {
-      tc::fence_after_sync();
-      issue(0);
-    }
-    for (int j = 0; j < ntiles; ++j) {
-      if (Cfg::NBUF == 2 && tid == 0 && j + 1 < ntiles) issue(j + 1);
-      const int buf = j % Cfg::NBUF;
-      ok = mbar_wait_bounded(&bar[buf], phase[buf], HELM_DEVERR_MMA_WAIT) && ok;
-      phase[buf] ^= 1u;
-      tc::fence_after_sync();
-      // ---- epilogue: TMEM lane (tid mod 128) <-> virtual pixel qs + 128 j + lane ----
-      const int q = qs + 128 * j + (tid & 127);
-      const int y = q / a.Po, x = q - y * a.Po;
-      const bool valid = ok && q < qe && x < a.Wo;
-#pragma unroll 1
-      for (int ph = 0; ph < PH; ++ph) {
-        const int oy = PH == 4 ? 2 * y + (ph >> 1) : y, ox = PH == 4 ? 2 * x + (ph & 1) : x;
-        const long pix = (static_cast<long>(b) * a.Hout + oy) * a.Wout + ox;
-        const long pix2 = (static_cast<long>(b / a.add2_div) * a.Hout + oy) * a.Wout + ox;
-#pragma unroll 1
-        for (int c0 = 16 * chalf; c0 < COUT; c0 += 32) {
-          float v[16];
-          tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * Cfg::ACC + ph * COUT + c0, v);
-          if (!valid) continue;
-          if (a.yraw) {
-            float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          }
-          if (a.y) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
-              v[i] = a.act ? tc::softplus_fast(t) : t;
-            }
-            if (a.add1) {
-              const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                uint4 u = pp[h];
-                const bf16* e = reinterpret_cast<const bf16*>(&u);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
-              }
-            }
-            if (a.add2) {
-              const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                uint4 u = pp[h];
-                const bf16* e = reinterpret_cast<const bf16*>(&u);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
-              }
-            }
-            uint4 o[2];
-            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-            uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
-            dst[0] = o[0];
-            dst[1] = o[1];
-          }
-        }
-      }
-      tc::fence_before_sync();
-      ok = __syncthreads_and(ok) != 0;  // uniform: a timed-out wait stops every thread
-      if (Cfg::NBUF == 1 && tid == 0 && j + 1 < ntiles && ok) {
+      __syncwarp();
+    } else {
+      // ---- epilogues: TMEM lane (tid mod 128) <-> virtual pixel of M-tile mt ----
+      const int mt = MT == 2 ? chalf : 0;
+      for (int j = 0; j < nsteps; ++j) {
+        const uint32_t g = gstep + j, buf = g % Cfg::NBUF, use = g / Cfg::NBUF;
+        ok = mbar_wait_bounded(&full[buf], use & 1u, HELM_DEVERR_MMA_WAIT) && ok;
         tc::fence_after_sync();
-        issue(j + 1);
+        const int q = qs + 128 * (MT * j + mt) + (tid & 127);
+        const int y = q / a.Po, x = q - y * a.Po;
+        const bool valid = ok && q < qe && x < a.Wo;
+#pragma unroll 1
+        for (int ph = 0; ph < PH; ++ph) {
+          const int oy = PH == 4 ? 2 * y + (ph >> 1) : y, ox = PH == 4 ? 2 * x + (ph & 1) : x;
+          const long pix = (static_cast<long>(b) * a.Hout + oy) * a.Wout + ox;
+          const long pix2 = (static_cast<long>(b / a.add2_div) * a.Hout + oy) * a.Wout + ox;
+#pragma unroll 1
+          for (int c0 = MT == 2 ? 0 : 16 * chalf; c0 < COUT; c0 += (MT == 2 ? 16 : 32)) {
+            float v[16];
+            tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * Cfg::STEP + mt * Cfg::ACC + ph * COUT +
+                         c0,
+                     v);
+            if (!valid) continue;
+            if (a.yraw) {
+              float4* o = reinterpret_cast<float4*>(a.yraw + pix * COUT + c0);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+            if (a.y) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                float t = fmaf(v[i], sScale[c0 + i], sShift[c0 + i]);
+                v[i] = a.act ? tc::softplus_fast(t) : t;
+              }
+              if (a.add1) {
+                const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  uint4 u = pp[h];
+                  const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+                  for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+                }
+              }
+              if (a.add2) {
+                const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  uint4 u = pp[h];
+                  const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+                  for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
+                }
+              }
+              uint4 o[2];
+              __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              uint4* dst = reinterpret_cast<uint4*>(a.y + pix * COUT + c0);
+              dst[0] = o[0];
+              dst[1] = o[1];
+            }
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[buf]);   // this warp's reads of the buffer are done
       }
-      if (!ok) break;
     }
-    __syncthreads();  // this window buffer is re-staged two segments later
+    gstep += nsteps;
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok) != 0;   // uniform; the window is restaged by the next segment
   }
-  tc::cp_async_wait_all();   // no copy may still target shared memory at exit
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, Cfg::NCOLS);
 }
@@ -374,46 +378,33 @@ __global__ void k_pack_weights(const float* __restrict__ w, int Ci, int Co, int 
   }
 }
 
-template <int CS, int COUT, int TAPS, int PH = 1>
+template <int CS, int COUT, int TAPS, int PH = 1, int MTR = 2>
 int launch_t(const ConvArgs& a0, cudaStream_t st) {
-  using Cfg = ConvCfg<CS, COUT, TAPS, PH>;
+  using Cfg = ConvCfg<CS, COUT, TAPS, PH, MTR>;
   ConvArgs a = a0;
   const int nph = a.mode == HELM_CONV_S2 ? 4 : 1;
-  // window budget: one CTA per SM for the heavy-weight layers, two otherwise (register-
-  // limited to two anyway at 256 threads)
+  // window budget: one CTA per SM for the heavy-weight layers, two otherwise
   const size_t budget = Cfg::BBYTES > 40 * 1024 ? 200 * 1024 : 100 * 1024;
-  const size_t fixed = Cfg::BBYTES + 2 * COUT * 4 + 64;
+  const size_t fixed = Cfg::BBYTES + 2 * COUT * 4 + 128;
   const size_t plane_row = static_cast<size_t>(nph) * Cfg::G * 16;
   auto window_rows = [&](int segq) {
-    const int nt = (segq + 127) / 128;
+    const int nt = Cfg::MT * ((segq + 128 * Cfg::MT - 1) / (128 * Cfg::MT));   // whole steps
     int Lr = 128 * nt + (TAPS == 1 ? 0 : (a.mode == HELM_CONV_S2 || PH == 4 ? a.Po + 2 : 2 * a.Po + 2));
     return Lr | 1;
   };
-  // window sizing for `nw` buffers; two (the next segment prefetched) when they fit
-  auto size_for = [&](int nw) {
-    if (TAPS == 1) {
-      int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (nw * plane_row * 128));
-      tiles = std::max(1, std::min(tiles, 16));
-      a.seg_q = 128 * tiles;
-    } else {
-      int R = 1;
-      for (int r = 2; r <= std::min(a.Ho, 32); ++r)
-        if (fixed + nw * plane_row * window_rows(r * a.Po) <= budget) R = r;
-      a.seg_q = R * a.Po;
-    }
-    a.L = window_rows(a.seg_q);
-    a.nwin = nw;
-    return fixed + nw * plane_row * a.L;
-  };
-  // two buffers only where they cost no segment length (a shorter segment re-reads more
-  // halo rows, which measured slower than the lost overlap)
-  size_t smem = size_for(1);
-  const int q1 = a.seg_q;
-  const size_t smem2 = size_for(2);
-  if (a.seg_q == q1 && smem2 <= 227 * 1024)
-    smem = smem2;
-  else
-    smem = size_for(1);
+  if (TAPS == 1) {
+    int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (plane_row * 128));
+    tiles = std::max(1, std::min(tiles, 16));
+    a.seg_q = 128 * tiles;
+  } else {
+    int R = 1;
+    for (int r = 2; r <= std::min(a.Ho, 32); ++r)
+      if (fixed + plane_row * window_rows(r * a.Po) <= budget) R = r;
+    a.seg_q = R * a.Po;
+  }
+  a.L = window_rows(a.seg_q);
+  a.nwin = 1;
+  const size_t smem = fixed + plane_row * a.L;
   a.segs_per_img = helm::div_up(static_cast<long>(a.Ho) * a.Po, a.seg_q);
   a.nsegs = a.segs_per_img * a.B;
   if (smem > 227 * 1024) {
@@ -423,7 +414,7 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
   static int nsm = 0;
   static bool attr = false;
   if (!attr) {
-    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS, PH, MTR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    227 * 1024));
     int dev;
     cudaGetDevice(&dev);
@@ -431,11 +422,11 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     attr = true;
   }
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA), TMEM
-  // columns (512 per SM) and registers (at most two 256-thread CTAs below 128 registers)
+  // columns (512 per SM) and registers (at most two 288-thread CTAs below 113 registers)
   int per_sm = static_cast<int>((228 * 1024) / (smem + 1024));
   per_sm = std::max(1, std::min({per_sm, 512 / Cfg::NCOLS, 2}));
   const int grid = std::max(1, std::min(a.nsegs, nsm * per_sm));
-  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS, PH><<<grid, CONV_THREADS, smem, st>>>(a));
+  HELM_LAUNCH("k_conv_tc", st, k_conv_tc<CS, COUT, TAPS, PH, MTR><<<grid, CONV_THREADS, smem, st>>>(a));
   HELM_CHECK_LAUNCH("k_conv_tc");
   return HELM_OK;
 }
@@ -508,8 +499,10 @@ int conv_tc(const ConvLaunch& c, cudaStream_t st) {
     set_error("conv: no transposed tensor-core kernel for Cin=%d Cout=%d", c.Ci, c.Co);
     return HELM_EINVAL;
   }
-#define HELM_CONV_CASE(cs, co, tp) \
-  if (CS == cs && c.Co == co && taps == tp) return launch_t<cs, co, tp>(a, st);
+#define HELM_CONV_CASE(cs, co, tp)                                      \
+  if (CS == cs && c.Co == co && taps == tp)                            \
+    return c.mode == HELM_CONV_S2 ? launch_t<cs, co, tp, 1, 1>(a, st)  \
+                                  : launch_t<cs, co, tp>(a, st);
   HELM_CONV_CASE(16, 16, 9)
   HELM_CONV_CASE(16, 32, 9)
   HELM_CONV_CASE(32, 32, 9)

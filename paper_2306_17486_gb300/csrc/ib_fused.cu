@@ -13,10 +13,12 @@
 //      the depthwise 3x3 on CUDA cores (weights in registers) + BN1 + softplus -> BF16
 //      K-major A operand of the projection; projection MMAs accumulate over the chunks;
 //   3. epilogue BN2 + the identity skip read from the staged halo tile -> BF16 output.
-// The activations are rounded to BF16 at the same points as in the three-kernel path
-// (after the expansion and after the depthwise conv), so both give the same result up
-// to FP32 summation order.
+// The expanded activations are held in FP16 (three more mantissa bits than the BF16
+// tensor of the three-kernel path) so that the depthwise products run as packed HFMA2:
+// each row of three taps is summed in FP16, the three row sums in FP32.  The depthwise
+// output is rounded to BF16 as in the three-kernel path.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(IB_THREADS, 2) k_ib_fused(const IbArgs a) {
   uint8_t* sX = smem;
   uint8_t* sWe = sX + Cfg::X_BYTES;
   uint8_t* sWp = sWe + Cfg::WE_BYTES;
-  bf16* sH = reinterpret_cast<bf16*>(sWp + Cfg::WP_BYTES);
+  __half* sH = reinterpret_cast<__half*>(sWp + Cfg::WP_BYTES);
   uint8_t* sD = reinterpret_cast<uint8_t*>(sH) + Cfg::H_BYTES;
   float* sDW = reinterpret_cast<float*>(sD + Cfg::D_BYTES);      // [9][E]
   float* sS0 = sDW + 9 * E;
@@ -176,14 +178,14 @@ __global__ void __launch_bounds__(IB_THREADS, 2) k_ib_fused(const IbArgs a) {
           tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + (warp >> 2) * IB_EC + c0, v);
           if (p >= IB_NH) continue;
           uint4 o[2];
-          __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+          __half2* ob = reinterpret_cast<__half2*>(o);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int c = ch * IB_EC + c0 + 2 * i;
             float t0 = tc::softplus_fast(fmaf(v[2 * i], sS0[c], sB0[c]));
             float t1 = tc::softplus_fast(fmaf(v[2 * i + 1], sS0[c + 1], sB0[c + 1]));
             if (!in) t0 = t1 = 0.f;
-            ob[i] = __floats2bfloat162_rn(t0, t1);
+            ob[i] = __floats2half2_rn(t0, t1);
           }
           uint4* dst = reinterpret_cast<uint4*>(sH + p * IB_EPITCH + c0);
           dst[0] = o[0];
@@ -197,13 +199,15 @@ __global__ void __launch_bounds__(IB_THREADS, 2) k_ib_fused(const IbArgs a) {
         // column fastest: the 16-byte stores of a quarter-warp go to consecutive rows
         const int xx = tid % IB_TW, g = tid / IB_TW;
         const int cb = ch * IB_EC + 8 * g;
-        float w[9][8];
+        __half2 w[9][4];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
           const float4 lo = *reinterpret_cast<const float4*>(sDW + k * E + cb);
           const float4 hi = *reinterpret_cast<const float4*>(sDW + k * E + cb + 4);
-          w[k][0] = lo.x; w[k][1] = lo.y; w[k][2] = lo.z; w[k][3] = lo.w;
-          w[k][4] = hi.x; w[k][5] = hi.y; w[k][6] = hi.z; w[k][7] = hi.w;
+          w[k][0] = __floats2half2_rn(lo.x, lo.y);
+          w[k][1] = __floats2half2_rn(lo.z, lo.w);
+          w[k][2] = __floats2half2_rn(hi.x, hi.y);
+          w[k][3] = __floats2half2_rn(hi.z, hi.w);
         }
 #pragma unroll 1
         for (int yy = 0; yy < IB_TH; ++yy) {
@@ -212,16 +216,20 @@ __global__ void __launch_bounds__(IB_THREADS, 2) k_ib_fused(const IbArgs a) {
           for (int e = 0; e < 8; ++e) acc[e] = 0.f;
 #pragma unroll
           for (int dy = 0; dy < 3; ++dy) {
+            __half2 rs[4];   // FP16 sum of the row's three taps
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
               const uint4 u = *reinterpret_cast<const uint4*>(sH + ((yy + dy) * IB_HW + xx + dx) * IB_EPITCH + 8 * g);
-              const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+              const __half2* h2 = reinterpret_cast<const __half2*>(&u);
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float2 f = __bfloat1622float2(h2[e]);
-                acc[2 * e] = fmaf(w[dy * 3 + dx][2 * e], f.x, acc[2 * e]);
-                acc[2 * e + 1] = fmaf(w[dy * 3 + dx][2 * e + 1], f.y, acc[2 * e + 1]);
-              }
+              for (int e = 0; e < 4; ++e)
+                rs[e] = dx == 0 ? __hmul2(w[dy * 3][e], h2[e]) : __hfma2(w[dy * 3 + dx][e], h2[e], rs[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f = __half22float2(rs[e]);
+              acc[2 * e] += f.x;
+              acc[2 * e + 1] += f.y;
             }
           }
           uint4 o;

@@ -9,6 +9,10 @@
 //   coarse correction     ec = V_{l+1}(rc)  or the coarsest GMRES solve
 //   prolong and correct   u2 = u + I_H^h ec                   (Eq. 8)
 //   post-sweep            z  = u2 + dinv_l (r - S_l u2)
+// Since D_l dinv_l = omega_J, the kernels use the equivalent forms
+//   r - S_l u  = (1 - omega_J) r + sum_neighbours u
+//   z          = (1 - omega_J) u2 + dinv_l (r + sum_neighbours u2)
+// which need no mass array.
 //
 // Kernels (each stages its tiles into shared memory with TMA tiled loads whose
 // out-of-range elements are zero-filled, which is the Dirichlet padding):
@@ -38,10 +42,9 @@ constexpr int RC_TW = 32, RC_TH = 8;                        // coarse tile
 constexpr int RF_W = 2 * RC_TW + 4, RF_H = 2 * RC_TH + 4;   // fine halo tile (68 x 20)
 
 __global__ void __launch_bounds__(256) k_resid_restrict(const __grid_constant__ CUtensorMap mr,
-                                                        const float2* __restrict__ mass,
                                                         const float2* __restrict__ dinv, float2* __restrict__ rc,
                                                         int nx, int ny, const int* __restrict__ active,
-                                                        const float* __restrict__ rscale) {
+                                                        const float* __restrict__ rscale, float onemw) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   __shared__ alignas(128) float2 R[RF_H * RF_W];
@@ -75,12 +78,8 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const __grid_constant__ 
     if (ly < 1 || ly > RF_H - 2 || lx < 1 || lx > RF_W - 2) continue;
     const int gy = gy0 + ly, gx = gx0 + lx;
     float2 q = make_float2(0.f, 0.f);
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-      float2 m = mass[static_cast<long>(gy) * nx + gx];
-      float2 su = cmul(make_float2(4.f - m.x, -m.y), U[i]);
-      su = csub(su, cadd(cadd(U[i - RF_W], U[i + RF_W]), cadd(U[i - 1], U[i + 1])));
-      q = csub(R[i], su);
-    }
+    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx)
+      q = cadd(cscale(R[i], onemw), cadd(cadd(U[i - RF_W], U[i + RF_W]), cadd(U[i - 1], U[i + 1])));
     Q[i] = q;
   }
   __syncthreads();
@@ -109,11 +108,10 @@ constexpr int PE_W = PS_TW / 2 + 4, PE_H = PS_TH / 2 + 2;    // coarse e tile (3
 
 __global__ void __launch_bounds__(256) k_prolong_smooth(const __grid_constant__ CUtensorMap mr,
                                                         const __grid_constant__ CUtensorMap me,
-                                                        const float2* __restrict__ mass,
                                                         const float2* __restrict__ dinv, float2* __restrict__ z,
                                                         int nx, int ny, const int* __restrict__ active,
                                                         const float* __restrict__ rscale,
-                                                        const float2* __restrict__ zadd) {
+                                                        const float2* __restrict__ zadd, float onemw) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   __shared__ alignas(128) float2 R[PR_H * PR_W];
@@ -172,10 +170,8 @@ __global__ void __launch_bounds__(256) k_prolong_smooth(const __grid_constant__ 
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int i = ly * PR_W + lx + q;
-      float2 m = mass[gi + q];
-      float2 su = cmul(make_float2(4.f - m.x, -m.y), U[i]);
-      su = csub(su, cadd(cadd(U[i - PR_W], U[i + PR_W]), cadd(U[i - 1], U[i + 1])));
-      out[q] = cadd(U[i], cmul(dinv[gi + q], csub(R[i], su)));
+      const float2 nb = cadd(cadd(U[i - PR_W], U[i + PR_W]), cadd(U[i - 1], U[i + 1]));
+      out[q] = cadd(cscale(U[i], onemw), cmul(dinv[gi + q], cadd(R[i], nb)));
       if (zadd) out[q] = cadd(out[q], zadd[b * plane + gi + q]);
     }
     *reinterpret_cast<float4*>(z + b * plane + gi) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
@@ -621,14 +617,15 @@ void carve_vcycle(Carve& c, const helm_problem* p, int batch, VcycleScratch* s) 
 int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, const VcycleScratch& s,
                   const int* active, const float* rscale, cudaStream_t st, const float2* zadd) {
   const int L = p->mg.levels;
+  const float onemw = static_cast<float>(1.0 - p->mg.omega_jacobi);
   int rc;
   for (int l = 0; l + 1 < L; ++l) {
     const float2* rin = l == 0 ? r : s.rc[l];
     CUtensorMap m;
     if ((rc = make_c64_map(&m, rin, p->lnx[l], p->lny[l], batch, RF_W, RF_H))) return rc;
     dim3 grid(div_up(p->lnx[l + 1], RC_TW), div_up(p->lny[l + 1], RC_TH), batch);
-    HELM_LAUNCH("k_resid_restrict", st, k_resid_restrict<<<grid, 256, 0, st>>>(m, p->massSL[l], p->dinvSL[l], s.rc[l + 1], p->lnx[l], p->lny[l],
-                                           active, l == 0 ? rscale : nullptr));
+    HELM_LAUNCH("k_resid_restrict", st, k_resid_restrict<<<grid, 256, 0, st>>>(m, p->dinvSL[l], s.rc[l + 1], p->lnx[l], p->lny[l],
+                                           active, l == 0 ? rscale : nullptr, onemw));
     HELM_CHECK_LAUNCH("k_resid_restrict");
   }
   {
@@ -660,8 +657,8 @@ int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, 
     if ((rc = make_c64_map(&mr, rin, p->lnx[l], p->lny[l], batch, PR_W, PR_H))) return rc;
     if ((rc = make_c64_map(&me, s.ec[l + 1], p->lnx[l + 1], p->lny[l + 1], batch, PE_W, PE_H))) return rc;
     dim3 grid(div_up(p->lnx[l], PS_TW), div_up(p->lny[l], PS_TH), batch);
-    HELM_LAUNCH("k_prolong_smooth", st, k_prolong_smooth<<<grid, 256, 0, st>>>(mr, me, p->massSL[l], p->dinvSL[l], zout, p->lnx[l], p->lny[l], active,
-                                           l == 0 ? rscale : nullptr, l == 0 ? zadd : nullptr));
+    HELM_LAUNCH("k_prolong_smooth", st, k_prolong_smooth<<<grid, 256, 0, st>>>(mr, me, p->dinvSL[l], zout, p->lnx[l], p->lny[l], active,
+                                           l == 0 ? rscale : nullptr, l == 0 ? zadd : nullptr, onemw));
     HELM_CHECK_LAUNCH("k_prolong_smooth");
   }
   return HELM_OK;
