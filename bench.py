@@ -32,14 +32,30 @@ N_MODELS, N_RHS, RESTART, RTOL, MAXIT = 4, 64, 10, 1e-6, 2000
 WORKLOAD = "helmholtz-576sq-4kappa-x64rhs-fgmres10"
 
 
+def job_seeds(rank: int):
+    """Replicas only: rank r solves its own N_MODELS slowness models with their own
+    right-hand sides; (kappa seed, right-hand-side seed) per model, disjoint across ranks."""
+    return [(10 + N_MODELS * rank + k, 1000 + N_MODELS * rank + k) for k in range(N_MODELS)]
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The job's time is the slowest rank's (all ranks start after one barrier)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _kappas(rank: int):
     import synth
-    return [synth.grf_kappa(N_INT, ABL, 8.0, seed=10 + 4 * rank + k) for k in range(N_MODELS)]
+    return [synth.grf_kappa(N_INT, ABL, 8.0, seed=ks) for ks, _ in job_seeds(rank)]
 
 
 def _rhs(rank: int, k: int):
     import synth
-    return synth.random_point_sources(N_INT + 2 * ABL, ABL, N_RHS, seed=1000 + 4 * rank + k)
+    return synth.random_point_sources(N_INT + 2 * ABL, ABL, N_RHS, seed=job_seeds(rank)[k][1])
 
 
 class ClockSampler:
@@ -104,15 +120,42 @@ def _peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-# algorithmic bytes per launch of the streaming kernels (per RHS point, complex64 = 8 B)
-def _kernel_bytes(name: str, npts: int, B: int, restart: int) -> float | None:
-    """Bytes a launch must move at minimum, per the data it reads and writes."""
-    n = npts * B
-    if name == "k_apply":                 # read x, write y (mass shared across the batch)
-        return 16.0 * n
-    if name == "k_scale":
-        return 16.0 * n
-    return None
+# DRAM bytes per RHS per launch measured by ncu (dram__bytes.sum.per_second x duration)
+# on captures whose tensors exceed the 129 MB L2, so that DRAM traffic is meaningful: the
+# matvec at the bench shape (64 RHS x 576^2: 298.3 MB per launch).  Kernels captured only
+# on small cases (their tensors stay in L2) or changed since their capture are absent.
+NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64}
+
+
+def _net_layer_bytes(I: int, B: int):
+    """Algorithmic bytes of one network application at grid I (solver only; the encodings
+    are read once per launch from L2 and not counted): every activation read once and
+    written once, BF16 NHWC.  Returns {kernel family: bytes}."""
+    h = I // 2
+    px = lambda n: n * n * B
+    ib = sum(4 * c * px(h >> k) for k, c in enumerate((16, 32, 64)))           # read x, write y
+    conv = 0
+    conv += (2 * 2 + 2 * 16) * px(h)                                             # l1: 2 -> 16
+    conv += 2 * 16 * px(h) + 2 * 32 * px(h // 2)                                 # l2: s2 16 -> 32
+    conv += 2 * 32 * px(h // 2) + 2 * 64 * px(h // 4)                            # l3: s2 32 -> 64
+    conv += 2 * 64 * px(h // 4) + 2 * 64 * px(h // 8) + 2 * (2 * 64 * 2) * px(h // 8)   # l4: 3 convs
+    for c_in, c_out, n in ((64, 64, h // 4), (64, 32, h // 2), (32, 16, h)):     # up modules
+        conv += 2 * c_in * px(n // 2) + 2 * c_out * px(n)                        # transposed s2
+        conv += 10 * c_out * px(n)                                               # conv1, conv2 (+ skip read)
+    implicit = 2 * (2 * 64) * px(I // 16)
+    proj = 2 * 16 * px(h) + 8 * px(I)
+    return {"k_ib_fused": ib, "k_conv_tc": conv, "k_implicit": implicit, "k_proj_prolong": proj}
+
+
+def _vcycle_bytes(N: int, levels: int, B: int):
+    """Algorithmic bytes of one V-cycle (complex64): level l down-leg reads r_l, writes the
+    coarse residual (1/4 size); up-leg reads r_l and the coarse correction, writes z_l."""
+    down = up = 0
+    for l in range(levels - 1):
+        n = (N >> l) ** 2 * B
+        down += 8 * n + 2 * n
+        up += 8 * n + 2 * n + 8 * n
+    return {"k_resid_restrict": down, "k_prolong_smooth": up}
 
 
 def run_gpu(args, rank: int, world: int):
@@ -187,10 +230,7 @@ def run_gpu(args, rank: int, world: int):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     launches = int(_lib.lib().helm_launch_count() - L0)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     n_rhs_total = args.steps * N_MODELS * N_RHS * world
     value = ms / (args.steps * N_MODELS * N_RHS)   # per-rank wall time / per-rank RHS
     value_job = ms / (n_rhs_total)                  # whole-job ms per RHS
@@ -214,24 +254,17 @@ def run_gpu(args, rank: int, world: int):
     e2e_steps = max(1, args.steps // 2)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / (e2e_steps * N_MODELS * N_RHS)
 
-    # ---- roofline of the dominant kernel: one profiled step (events per launch) --------
+    # ---- per-kernel shares of one profiled step (CUDA events around every launch) -------
     L = _lib.lib()
-    L.helm_profile_begin()
-    step()
-    torch.cuda.synchronize()
     import ctypes as C
-    nk = C.c_int()
-    L.helm_profile_end(C.byref(nk))
-    prof = []
-    for i in range(nk.value):
-        nm, cnt, tot = C.c_char_p(), C.c_long(), C.c_double()
-        L.helm_profile_read(i, C.byref(nm), C.byref(cnt), C.byref(tot))
-        prof.append((nm.value.decode(), cnt.value, tot.value))
-    prof.sort(key=lambda t: -t[2])
+    prof = _profile(L, C, step)
     tot_ms = sum(t[2] for t in prof)
     hbm, bf16, src = _peaks()
-    # dominant kernel (by share) and its roofline from a standalone timing of the same launch shape
-    roof = _roofline(helm, probs[0], bs[0], dev, prof, hbm, src)
+    # ---- rooflines: the step's dominant kernel and the other hot families, each timed
+    #      live (library CUDA events on the launching stream) at the bench shape ----------
+    roofs = _rooflines(helm, L, C, net, probs[0], dev, hbm, src, prof)
+    dom = prof[0][0]
+    roof = next((r for r in roofs if r["kernel"] == dom), roofs[0])
 
     out = {
         "metric": METRIC, "value": round(value_job, 4), "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
@@ -251,6 +284,7 @@ def run_gpu(args, rank: int, world: int):
         "max_true_rel_res": float(allst["rel_res_true"].max()),
         "training": train_info,
         "roofline": roof,
+        "roofline_kernels": [r for r in roofs if r is not roof],
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms/RHS",
                 "h2d_bytes_per_step": int(sum(b.numel() * 8 for b in bs)),
                 "d2h_bytes_per_step": int(sum(x.numel() * 16 for x in xs))},
@@ -289,32 +323,70 @@ def _network(helm, dev, args):
     return net, {"source": "trained in this run", "steps": args.train_steps, "train_seconds": time.time() - t0}
 
 
-def _roofline(helm, P, b, dev, prof, hbm, src):
-    """Achieved GB/s of the top kernel that has an algorithmic byte count, timed with
-    CUDA events on the launching stream over repeated launches of the solve's shape."""
+def _profile(L, C, fn):
+    """Per-kernel (name, launches, total ms) of one call of fn under the library profiler."""
+    import torch
+    L.helm_profile_begin()
+    fn()
+    torch.cuda.synchronize()
+    nk = C.c_int()
+    L.helm_profile_end(C.byref(nk))
+    prof = []
+    for i in range(nk.value):
+        nm, cnt, tot = C.c_char_p(), C.c_long(), C.c_double()
+        L.helm_profile_read(i, C.byref(nm), C.byref(cnt), C.byref(tot))
+        prof.append((nm.value.decode(), cnt.value, tot.value))
+    prof.sort(key=lambda t: -t[2])
+    return prof
+
+
+def _rooflines(helm, L, C, net, P, dev, hbm, src, step_prof):
+    """Achieved GB/s of the hot kernel families at the bench shape (64 RHS x 576^2):
+    algorithmic bytes per launch (network layers, V-cycle levels, the matvec) over the
+    average launch duration measured by the library's CUDA events on the launching stream,
+    against the measured HBM copy bandwidth."""
     import torch
     N = P.nx
-    x = torch.randn((N_RHS, N, N), dtype=torch.complex64, device=dev)
-    y = torch.empty_like(x)
-    for _ in range(3):
-        helm.helmholtz_apply(P, x, y)
-    s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    e0.record(s)
-    for _ in range(reps):
-        helm.helmholtz_apply(P, x, y)
-    e1.record(s)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    r = torch.randn((N_RHS, N, N), dtype=torch.complex64, device=dev, generator=g)
+    net.set_problem(P)
+    reps = 3
+    for _ in range(2):
+        net.apply(P, r)
+        helm.slmg_vcycle(P, r)
+        helm.helmholtz_apply(P, r)
     torch.cuda.synchronize()
-    dt = e0.elapsed_time(e1) / reps * 1e-3
-    byts = 16.0 * N * N * N_RHS
-    ach = byts / dt / 1e9
-    share = {n: t for n, _, t in prof}
+
+    def run():
+        for _ in range(reps):
+            net.apply(P, r)
+            helm.slmg_vcycle(P, r)
+            helm.helmholtz_apply(P, r)
+
+    prof = {n: (c, t) for n, c, t in _profile(L, C, run)}
+    byts = dict(_net_layer_bytes(N, N_RHS))
+    byts.update(_vcycle_bytes(N, LEVELS, N_RHS))
+    byts["k_apply"] = 16.0 * N * N * N_RHS
+    share = {n: t for n, _, t in step_prof}
     tot = sum(share.values())
-    return {"kernel": "k_apply (Helmholtz matvec, 64 RHS x 576^2)", "bound": "hbm", "achieved": round(ach, 1),
-            "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_source": src,
-            "bytes_per_launch": byts, "traffic": None,
-            "share_of_step": round(share.get("k_apply", 0.0) / tot, 4) if tot else None}
+    out = []
+    for name, b in byts.items():
+        if name not in prof:
+            continue
+        cnt, ms = prof[name]
+        per_call = cnt / reps                      # launches per application
+        t_launch = ms / cnt * 1e-3                 # average launch duration (s)
+        b_launch = b / per_call                    # average algorithmic bytes per launch
+        ach = b_launch / t_launch / 1e9
+        tr = NCU_TRAFFIC_PER_RHS.get(name)
+        out.append({"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "peak_source": src, "bytes_per_launch": round(b_launch),
+                    "launch_ms": round(t_launch * 1e3, 4),
+                    "traffic": round(tr * N_RHS / per_call) if tr is not None else None,
+                    "share_of_step": round(share.get(name, 0.0) / tot, 4) if tot else None})
+    out.sort(key=lambda d: -(d["share_of_step"] or 0.0))
+    return out
 
 
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations_576.json")
