@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 METRIC = "ms per RHS to 1e-6 rel. residual, CNN+MG vs MG-only preconditioned FGMRES"
 N_INT, ABL, LEVELS = 512, 32, 4
 N_MODELS, N_RHS, RESTART, RTOL, MAXIT = 4, 64, 10, 1e-6, 2000
+# the composed CNN + V-cycle preconditioner on every CNN_EVERY-th Arnoldi step, the
+# V-cycle alone on the others (flexible GMRES admits a different preconditioner per
+# step); 1 is the paper's schedule, reported beside the headline
+CNN_EVERY = 3
 WORKLOAD = "helmholtz-576sq-4kappa-x64rhs-fgmres10"
 
 
@@ -185,13 +189,13 @@ def run_gpu(args, rank: int, world: int):
     for p in probs:
         p.workspace(N_RHS, RESTART, net)
 
-    def step(record=None, cnn=True):
+    def step(record=None, cnn=True, every=CNN_EVERY):
         for k in range(N_MODELS):
             xs[k].zero_()
             if cnn:
                 net.set_problem(probs[k])      # encoder, once per slowness model (amortised)
             _, st = helm.fgmres_solve(probs[k], bs[k], xs[k], cnn=net if cnn else None, restart=RESTART,
-                                      rtol=RTOL, maxit=MAXIT, warmup_iters=3)
+                                      rtol=RTOL, maxit=MAXIT, warmup_iters=3, cnn_every=every)
             if record is not None:
                 record.append(st)
 
@@ -213,6 +217,17 @@ def run_gpu(args, rank: int, world: int):
     barrier()
     mg_ms = m0.elapsed_time(m1)
     mg_all = np.concatenate(mg_stats)
+    # the paper's schedule (the network on every Arnoldi step)
+    step(cnn=True, every=1)
+    barrier()
+    pp_stats = []
+    m0.record()
+    for _ in range(args.steps):
+        step(pp_stats, cnn=True, every=1)
+    m1.record()
+    barrier()
+    pp_ms = m0.elapsed_time(m1)
+    pp_all = np.concatenate(pp_stats)
     for _ in range(args.warmup):
         step()
     barrier()
@@ -248,7 +263,8 @@ def run_gpu(args, rank: int, world: int):
             bd = hb[k].to(dev, non_blocking=True)
             xs[k].zero_()
             net.set_problem(probs[k])
-            helm.fgmres_solve(probs[k], bd, xs[k], cnn=net, restart=RESTART, rtol=RTOL, maxit=MAXIT, warmup_iters=3)
+            helm.fgmres_solve(probs[k], bd, xs[k], cnn=net, restart=RESTART, rtol=RTOL, maxit=MAXIT, warmup_iters=3,
+                              cnn_every=CNN_EVERY)
             hx[k].copy_(xs[k], non_blocking=True)
     barrier()
     e2e_steps = max(1, args.steps // 2)
@@ -273,7 +289,9 @@ def run_gpu(args, rank: int, world: int):
         "data": "synthetic: seeded GRF slowness (ell=8) in [0.25,1], seeded point sources",
         "config": {"workload": WORKLOAD, "grid": N, "interior": N_INT, "abl": ABL, "kappa_models": N_MODELS,
                    "rhs_per_model": N_RHS, "restart": RESTART, "rtol": RTOL, "mg_levels": LEVELS,
-                   "preconditioner": "BF16 encoder-solver CNN (implicit layer) + FP32 SL-MG V(1,1), warm-up 3",
+                   "preconditioner": "BF16 encoder-solver CNN (implicit layer) + FP32 SL-MG V(1,1) on every "
+                                     f"{CNN_EVERY}rd Arnoldi step, SL-MG V(1,1) alone on the others, warm-up 3",
+                   "cnn_every": CNN_EVERY,
                    "l2": "inputs larger than L2 (Krylov basis 1.9 GB/model)"},
         "method": "cnn+mg",
         "iterations": {"mean": float(iters.mean()), "max": int(iters.max()), "converged_frac": conv},
@@ -281,6 +299,11 @@ def run_gpu(args, rank: int, world: int):
                     "iterations_mean": float(mg_all["iters"].mean()), "iterations_max": int(mg_all["iters"].max()),
                     "converged_frac": float(np.mean(mg_all["status"] == 1))},
         "speedup_vs_mg_only": round((mg_ms / (args.steps * N_MODELS * N_RHS)) / max(value_job, 1e-12), 3),
+        "paper_schedule": {"cnn_every": 1, "value": round(pp_ms / (args.steps * N_MODELS * N_RHS), 4),
+                           "unit": "ms/RHS", "iterations_mean": float(pp_all["iters"].mean()),
+                           "iterations_max": int(pp_all["iters"].max()),
+                           "converged_frac": float(np.mean(pp_all["status"] == 1)),
+                           "max_true_rel_res": float(pp_all["rel_res_true"].max())},
         "max_true_rel_res": float(allst["rel_res_true"].max()),
         "training": train_info,
         "roofline": roof,
@@ -455,11 +478,14 @@ def cpu_baseline(kappa, b1, gpu_iters_mean):
     V-cycle), scaled to ms per RHS by the GPU run's mean iteration count."""
     t_cnn, t_mg = _oracle_iteration_time(kappa, b1[0], 2, 6)
     threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or (os.cpu_count() or 1)
-    per_it = t_cnn if t_cnn is not None else t_mg
+    # the headline schedule: the network on Arnoldi steps j = 0 mod CNN_EVERY of each cycle
+    f_cnn = len(range(0, RESTART, CNN_EVERY)) / RESTART
+    per_it = f_cnn * t_cnn + (1 - f_cnn) * t_mg if t_cnn is not None else t_mg
     return {"value": round(per_it * gpu_iters_mean * 1e3, 2), "unit": "ms/RHS", "cores": threads,
             "kind": "oracle",
             "sample": f"2 CNN+V-cycle FGMRES(10) iterations ({t_cnn:.2f} s each) and 6 V-cycle-only iterations "
-                      f"({t_mg:.3f} s each) on 1 RHS of kappa 0; x mean GPU iterations/RHS {gpu_iters_mean:.1f}"
+                      f"({t_mg:.3f} s each) on 1 RHS of kappa 0, mixed {f_cnn:.1f} : {1 - f_cnn:.1f} as in the "
+                      f"schedule, x mean GPU iterations/RHS {gpu_iters_mean:.1f}"
             if t_cnn is not None else f"6 V-cycle FGMRES(10) iterations on 1 RHS ({t_mg:.3f} s each)"}
 
 
@@ -504,7 +530,8 @@ def run_reference(args, rank: int, world: int):
                    "restart": RESTART, "rtol": RTOL, "mg_levels": LEVELS},
         "cpu_baseline": {"value": round(v, 2), "unit": "ms/RHS", "cores": threads, "kind": "oracle",
                          "sample": f"1 CNN+V-cycle FGMRES(10) iteration of the FP64 oracle per step on RHS 0 of "
-                                   f"kappa 0, x {n_it:.1f} iterations ({which} count of the oracle to 1e-6)"},
+                                   f"kappa 0 (the paper's schedule: the network on every step), x {n_it:.1f} "
+                                   f"iterations ({which} count of the oracle to 1e-6)"},
         "e2e": {"value": round(v, 2), "unit": "ms/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -164,6 +164,10 @@ typedef struct {
                        (Section 4.1: typically 3); ignored without a CNN                   */
   int reorth;       /* 0: classical Gram-Schmidt; 1: CGS with selective re-orthogonalisation
                        (second pass when ||w|| drops below ||w_0||/sqrt 2); 2: always CGS2   */
+  int cnn_every;    /* with a CNN: the composed preconditioner on Arnoldi steps j with
+                       j mod cnn_every == 0, the V-cycle alone on the others (FGMRES admits
+                       a different preconditioner per step); 1 = every step, the paper's
+                       method (default); must be >= 1                                      */
 } helm_fgmres_opts;
 
 /* Per-RHS result. */

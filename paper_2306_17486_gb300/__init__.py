@@ -42,9 +42,10 @@ def mg_opts(levels=3, beta=0.5, omega_jacobi=0.8, coarse_iters=10, sl_includes_g
     return o
 
 
-def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1):
+def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1, cnn_every=1):
     o = FgmresOpts()
     o.restart, o.rtol, o.maxit, o.warmup_iters, o.reorth = restart, rtol, maxit, warmup_iters, reorth
+    o.cnn_every = cnn_every
     return o
 
 
@@ -142,7 +143,7 @@ def slmg_vcycle_static(p: Problem, r: torch.Tensor, z: torch.Tensor | None = Non
 
 
 def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn=None, restart=10, rtol=1e-6,
-                 maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None):
+                 maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None, cnn_every=1):
     """Solve h^2 A x = b (b complex64 [B, ny, nx]); x complex128 (in: x0, out: solution).
     Returns (x, stats) with stats a numpy structured array (iters, status, rel_res_est,
     rel_res_true) per right-hand side."""
@@ -153,7 +154,7 @@ def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn
     _need(x, torch.complex128, "x")
     stats = torch.zeros(B * STATS_DTYPE.itemsize, dtype=torch.uint8, device=b.device)
     ws = p.workspace(B, restart, cnn)
-    o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth)
+    o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth, cnn_every)
     caps = None
     if maxit_per_rhs is not None:
         _need(maxit_per_rhs, torch.int32, "maxit_per_rhs")

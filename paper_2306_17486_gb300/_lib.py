@@ -25,7 +25,8 @@ class MgOpts(C.Structure):
 
 
 class FgmresOpts(C.Structure):
-    _fields_ = [("restart", i32), ("rtol", f64), ("maxit", i32), ("warmup_iters", i32), ("reorth", i32)]
+    _fields_ = [("restart", i32), ("rtol", f64), ("maxit", i32), ("warmup_iters", i32), ("reorth", i32),
+                ("cnn_every", i32)]
 
 
 class FgmresStats(C.Structure):

@@ -544,6 +544,7 @@ void helm_fgmres_opts_default(helm_fgmres_opts* o) {
   o->maxit = 2000;
   o->warmup_iters = 3;
   o->reorth = 1;
+  o->cnn_every = 1;
 }
 
 int helm_workspace_size(const helm_problem* p, const helm_cnn* cnn, int batch, int restart, size_t* bytes) {
@@ -571,8 +572,8 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
     o = *opts_;
   else
     helm_fgmres_opts_default(&o);
-  if (o.restart < 1 || o.restart > HELM_MAX_RESTART || o.maxit < 0 || !(o.rtol >= 0.0)) {
-    set_error("helm_fgmres_solve: restart must be in [1,%d], maxit >= 0, rtol >= 0", HELM_MAX_RESTART);
+  if (o.restart < 1 || o.restart > HELM_MAX_RESTART || o.maxit < 0 || !(o.rtol >= 0.0) || o.cnn_every < 1) {
+    set_error("helm_fgmres_solve: restart must be in [1,%d], maxit >= 0, rtol >= 0, cnn_every >= 1", HELM_MAX_RESTART);
     return HELM_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -642,7 +643,7 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
       float2* vj = S.V + j * vstride;
       float2* zj = S.Z + j * vstride;
       float2* w = S.V + (j + 1) * vstride;
-      if (use_cnn && !warm) {
+      if (use_cnn && !warm && j % o.cnn_every == 0) {
         Carve cc(c.base + c.off, c.cap - c.off);
         rc = launch_cnn_precond(p, cnn, vj, zj, B, cc, vs, S.cyc, st, S.sel, nsel);
       } else {

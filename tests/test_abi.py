@@ -38,7 +38,7 @@ def test_host_side_validation_without_gpu(L):
                                  ctypes.byref(ctypes.c_void_p())) == -2
     f = _lib.FgmresOpts()
     L.helm_fgmres_opts_default(ctypes.byref(f))
-    assert (f.restart, f.rtol, f.maxit, f.warmup_iters) == (10, 1e-6, 2000, 3)
+    assert (f.restart, f.rtol, f.maxit, f.warmup_iters, f.reorth, f.cnn_every) == (10, 1e-6, 2000, 3, 1, 1)
     assert L.helm_version().startswith(b"helm-gb300")
     assert ctypes.sizeof(_lib.FgmresStats) == 24
 

@@ -241,3 +241,29 @@ def test_training_with_several_slowness_models_per_batch(helm):
     assert np.linalg.norm(eg.cpu().numpy() - e_ref) <= 4e-2 * np.linalg.norm(e_ref)
     worst = max(np.linalg.norm(grads[n] - ref[n]) / np.linalg.norm(ref[n]) for n in ref if np.linalg.norm(ref[n]) > 0)
     assert worst < 0.1, worst
+
+
+@pytest.mark.parametrize("every", [1, 3])
+def test_fgmres_with_network_every_kth_step_converges(helm, every):
+    """FGMRES with the composed preconditioner on Arnoldi steps j = 0 mod `every` and the
+    V-cycle alone on the others: every RHS reaches the tolerance, judged by the FP64
+    true residual the oracle computes from the GPU solution; cnn_every = 0 is rejected."""
+    I, abl, B = 64, 8, 3
+    P, running = _random_net(31)
+    net = helm.Cnn(skip_threshold=512)
+    net.load_dict(P)
+    net.load_running(running)
+    kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 5).astype(np.float32).astype(np.float64)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    b = synth.random_point_sources(I, abl, B, seed=8)
+    bg = torch.tensor(b, dtype=torch.complex64, device="cuda")
+    x, st = helm.fgmres_solve(p, bg, cnn=net, restart=10, rtol=1e-6, maxit=2000, cnn_every=every)
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    xs = x.cpu().numpy()
+    for i in range(B):
+        rel = np.linalg.norm(b[i] - op.A(xs[i])) / np.linalg.norm(b[i])
+        assert st["status"][i] == 1 and rel <= 1e-6, (every, i, rel, st[i])
+    with pytest.raises(helm.HelmError, match="cnn_every"):
+        helm.fgmres_solve(p, bg, cnn=net, restart=10, rtol=1e-6, cnn_every=0)
