@@ -23,18 +23,24 @@ def omega_h_for_ppw(kappa_max: float = 1.0, ppw: float = 10.0) -> float:
     return 2.0 * np.pi / (ppw * kappa_max)
 
 
-def abl_gamma(N: int, abl: int, gamma0: float = 0.0) -> np.ndarray:
-    """Attenuation field gamma(x) = gamma0 + gamma_ABL(x) on an N x N grid.
+def _abl_profile(N: int, abl: int) -> np.ndarray:
+    i = np.arange(N)
+    d = np.maximum(np.maximum(abl - i, i - (N - 1 - abl)), 0).astype(np.float64)
+    return (d / abl) ** 2 if abl > 0 else np.zeros(N)
+
+
+def abl_gamma(N: int, abl: int, gamma0: float = 0.0, M: int | None = None) -> np.ndarray:
+    """Attenuation field gamma(x) = gamma0 + gamma_ABL(x) on an N x M grid (rows x
+    columns; M = N by default).
 
     Section 3.1: the absorbing boundary layer is a function in gamma that goes
     from 0 to 1 towards the boundaries.  Reading: with d = distance in cells into
     the layer (0 at the first interior index `abl`, `abl` at the outermost cell),
     gamma_ABL = max((d_x/L)^2, (d_y/L)^2).
     """
-    i = np.arange(N)
-    d = np.maximum(np.maximum(abl - i, i - (N - 1 - abl)), 0).astype(np.float64)
-    prof = (d / abl) ** 2 if abl > 0 else np.zeros(N)
-    return gamma0 + np.maximum(prof[:, None], prof[None, :])
+    py = _abl_profile(N, abl)
+    px = py if M is None or M == N else _abl_profile(M, abl)
+    return gamma0 + np.maximum(py[:, None], px[None, :])
 
 
 def helmholtz_mass(kappa: np.ndarray, omega_h: float, gamma: np.ndarray) -> np.ndarray:
@@ -83,7 +89,8 @@ def apply_stencil_loops(mass: np.ndarray, x: np.ndarray) -> np.ndarray:
 class Problem:
     """One slowness model with its frequency and absorbing layer.
 
-    kappa   : float64 [N][N] slowness (including the absorbing layer cells)
+    kappa   : float64 [ny][nx] slowness (including the absorbing layer cells); square
+              (the paper's setting) or rectangular with square cells
     abl     : layer width in cells
     omega_h : omega * h (dimensionless); default from the 10 points-per-wavelength rule
     gamma0  : constant attenuation (0 at solve time, 0.05 when generating training
@@ -93,11 +100,11 @@ class Problem:
     def __init__(self, kappa: np.ndarray, abl: int, omega_h: float | None = None,
                  gamma0: float = 0.0):
         self.kappa = np.asarray(kappa, dtype=np.float64)
-        self.N = self.kappa.shape[0]
-        assert self.kappa.shape == (self.N, self.N)
+        assert self.kappa.ndim == 2
+        self.N, self.M = self.kappa.shape
         self.abl = abl
         self.omega_h = omega_h_for_ppw(self.kappa.max()) if omega_h is None else omega_h
-        self.gamma = abl_gamma(self.N, abl, gamma0)
+        self.gamma = abl_gamma(self.N, abl, gamma0, self.M)
         self.mass_A = helmholtz_mass(self.kappa, self.omega_h, self.gamma)
 
     def A(self, x: np.ndarray) -> np.ndarray:

@@ -151,3 +151,25 @@ def test_coarse_gmres_jacobi_converges_to_lu():
     res10 = np.linalg.norm(r - hz.apply_stencil(mass, x10))
     res5 = np.linalg.norm(r - hz.apply_stencil(mass, mg.gmres_jacobi_fixed(mass, r, 5)))
     assert res10 < res5 < np.linalg.norm(r)
+
+
+def test_rectangular_grids_reduce_to_the_square_definitions():
+    """Rectangular grids (square cells): each axis of gamma is the square profile of its
+    own length, the stencil equals the element-by-element brute force, and FGMRES with
+    the V-cycle solves the assembled system (dense LU) on a small rectangular grid."""
+    from oracle import fgmres as ofg
+    N, M, L = 24, 40, 4
+    g = hz.abl_gamma(N, L, 0.0, M)
+    assert g.shape == (N, M)
+    assert np.array_equal(g[N // 2], hz.abl_gamma(M, L)[M // 2])      # row through the middle
+    assert np.array_equal(g[:, M // 2], hz.abl_gamma(N, L)[:, N // 2])
+    rng = np.random.default_rng(4)
+    kappa = 0.25 + 0.75 * rng.random((N, M))
+    p = hz.Problem(kappa, L)
+    x = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    assert np.allclose(p.A(x), hz.apply_stencil_loops(p.mass_A, x), atol=1e-13)
+    b = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    mgp = mg.SLMultigrid(p, 3, coarse="lu")
+    xs, res = ofg.fgmres(p.A, b, np.zeros_like(b), mgp, 20, 1e-12, 400)
+    ref = np.linalg.solve(mg.dense_matrix(p.mass_A), b.ravel()).reshape(N, M)
+    assert np.linalg.norm(xs - ref) <= 1e-9 * np.linalg.norm(ref)
