@@ -165,6 +165,33 @@ class Trainer:
         self.history = [tuple(h) for h in d["history"]]
 
 
+def retrain(net: Cnn, problem: Problem, steps: int = 300, batch: int = 32, lr: float = 1e-4, seed: int = 0,
+            log=None) -> list:
+    """Solve-time re-training on one (out-of-distribution) slowness model (Section 5:
+    the pre-trained network is optimised for a short time on the problem at hand):
+    Adam on Eq. (17) pairs generated from `problem` by the plain solver, batches of
+    `batch` samples of that single model, constant learning rate.  `problem` must be
+    built with gamma0 = 0.05 as in the training data (Section 4.3).  Returns the losses."""
+    gen = torch.Generator(device=problem.device)
+    gen.manual_seed(seed)
+    opt = Adam(net.params, lr=lr)
+    N = problem.nx
+    losses = []
+    for i in range(steps):
+        x = smooth_plus_noise(batch, N, gen, device=problem.device)
+        k = torch.randint(2, 21, (batch,), generator=gen, device=problem.device, dtype=torch.int32)
+        e, r = datagen_pairs(problem, x, k, max_iters=20, normalise=True)
+        e_pred = net.forward_train([problem], r)
+        loss, g = mse_loss(e_pred, e)
+        grads = net.backward([problem], g)
+        opt.step(grads)
+        net.set_params()
+        losses.append(loss)
+        if log and (i + 1) % 50 == 0:
+            log(f"retrain step {i + 1}: loss {float(torch.stack(losses[-50:]).mean()):.4f}")
+    return [float(v) for v in losses]
+
+
 def save_weights(net: Cnn, path: str, meta: dict | None = None):
     """Trained network for inference: FP32 parameters and BN running statistics."""
     np.savez(path, params=net.params.cpu().numpy(), running=net.running_dict_flat(),

@@ -69,6 +69,29 @@ def layered_grf_kappa(n: int, abl: int, seed: int = 0) -> np.ndarray:
     return _embed_abl(_to_range(0.5 * a + 0.5 * b), abl)
 
 
+def salt_kappa(n: int, abl: int, seed: int = 0) -> np.ndarray:
+    """Out-of-distribution stand-in for a salt-dome model: a smooth layered background
+    (slowness decreasing with depth, i.e. velocity increasing, with 6 random
+    interfaces) holding a high-velocity body (slowness 0.25) bounded by a random smooth
+    closed curve, Gaussian-smoothed with sigma 1 and renormalised to [0.25, 1].  Sharper
+    contrast and larger features than the training fields.  Returns float64 [N][N]."""
+    rng = np.random.default_rng(seed)
+    y = np.linspace(0.0, 1.0, n)[:, None] * np.ones((1, n))
+    depths = np.sort(rng.uniform(0.1, 0.9, size=6))
+    values = np.sort(rng.uniform(0.45, 1.0, size=7))[::-1]
+    f = np.full((n, n), values[0])
+    for d, v in zip(depths, values[1:]):
+        f = np.where(y >= d, v, f)
+    yy, xx = np.mgrid[0:n, 0:n] / (n - 1.0)
+    cy, cx = rng.uniform(0.35, 0.55), rng.uniform(0.35, 0.65)
+    th = np.arctan2(yy - cy, xx - cx)
+    rad = 0.18 + 0.04 * np.sin(3 * th + rng.uniform(0, 2 * np.pi)) + 0.03 * np.cos(5 * th + rng.uniform(0, 2 * np.pi))
+    body = np.hypot(yy - cy, (xx - cx) * 0.7) < rad
+    f = np.where(body, KAPPA_MIN, f)
+    f = gaussian_filter(f, sigma=1.0, mode="nearest")
+    return _embed_abl(_to_range(f), abl)
+
+
 def centre_source(N: int) -> np.ndarray:
     """h^2-scaled right-hand side of a unit point source at the grid centre:
     h^2 g = 1 at node (N//2, N//2).  complex128 [N][N]."""

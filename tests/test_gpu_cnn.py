@@ -267,3 +267,24 @@ def test_fgmres_with_network_every_kth_step_converges(helm, every):
         assert st["status"][i] == 1 and rel <= 1e-6, (every, i, rel, st[i])
     with pytest.raises(helm.HelmError, match="cnn_every"):
         helm.fgmres_solve(p, bg, cnn=net, restart=10, rtol=1e-6, cnn_every=0)
+
+
+def test_retraining_on_one_slowness_model_reduces_the_loss(helm):
+    """Solve-time re-training (Section 5, out-of-distribution models): a few Adam steps on
+    Eq. (17) pairs of one salt-body model lower the Eq. (16) loss, and the BN running
+    statistics move to that model (the network's output changes)."""
+    from paper_2306_17486_gb300 import train as T
+    net = helm.Cnn(skip_threshold=256)
+    net.load_dict(synth.random_params(T.init_spec(net), seed=0))
+    kap = synth.salt_kappa(96, 16, seed=1)
+    kt = torch.tensor(kap, dtype=torch.float32, device="cuda")
+    oh = 2 * np.pi / 10 / float(kap.max())
+    p = helm.Problem(kt, 16, oh, gamma0=0.05, levels=3)
+    r = torch.tensor(synth.random_complex((2, 128, 128), 3), dtype=torch.complex64, device="cuda")
+    net.set_problem(p)
+    e0 = net.apply(p, r).clone()
+    losses = T.retrain(net, p, steps=40, batch=8, lr=1e-3, seed=2)
+    assert np.mean(losses[-10:]) < np.mean(losses[:10]), losses
+    net.set_problem(p)
+    e1 = net.apply(p, r)
+    assert torch.isfinite(e1).all() and (e1 - e0).abs().max() > 0
