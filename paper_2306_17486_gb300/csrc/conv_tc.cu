@@ -20,9 +20,10 @@
 //                   flipped kernel that reach it (out(2y+py, 2x+px) sums in(y + a, x + c)
 //                   over a in {0, py}, c in {0, px}); no zero-inserted copy is staged
 //   1x1           : 128 consecutive pixels, Po = Wo
-// One thread issues all MMAs of a tile and commits them to an mbarrier; 8 warps read
-// the accumulator with tcgen05.ld (TMEM lane t = pixel q0 + t) and run the epilogue.
-// CTAs are persistent over tiles; weights stay resident in shared memory.
+// A dedicated MMA warp issues all MMAs of a step and commits them to an mbarrier; 8
+// epilogue warps read the accumulator with tcgen05.ld (TMEM lane t = pixel q0 + t) and
+// run the epilogue (see k_conv_tc).  CTAs are persistent over segments; weights stay
+// resident in shared memory.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -52,7 +53,6 @@ struct ConvArgs {
   int seg_q;             // virtual output pixels per segment (whole rows for 3x3)
   int segs_per_img, nsegs;
   int L;                 // window rows per plane (odd)
-  int nwin;              // window buffers: 2 (next segment prefetched) or 1
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -403,7 +403,6 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     a.seg_q = R * a.Po;
   }
   a.L = window_rows(a.seg_q);
-  a.nwin = 1;
   const size_t smem = fixed + plane_row * a.L;
   a.segs_per_img = helm::div_up(static_cast<long>(a.Ho) * a.Po, a.seg_q);
   a.nsegs = a.segs_per_img * a.B;

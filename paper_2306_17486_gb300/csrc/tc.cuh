@@ -103,9 +103,6 @@ __device__ __forceinline__ void cp_async_small(uint32_t dst, const void* src, ui
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most one (the most recent) commit group of this thread is pending
-__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(__expf(-fabsf(x))); }
 // log(1 + exp(-|x|)) through the fast exp/log units: absolute error below 1e-6, far
