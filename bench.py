@@ -204,7 +204,7 @@ def run_gpu(args, rank: int, world: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # SL-MG-only arm (the comparison and the judge of the learned preconditioner)
+    # SL-MG-only arm (what the learned preconditioner is compared with)
     for _ in range(max(1, args.warmup // 2)):
         step(cnn=False)
     barrier()
