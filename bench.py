@@ -124,11 +124,12 @@ def _peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-# DRAM bytes per RHS per launch measured by ncu (dram__bytes.sum.per_second x duration)
-# on captures whose tensors exceed the 129 MB L2, so that DRAM traffic is meaningful: the
-# matvec at the bench shape (64 RHS x 576^2: 298.3 MB per launch).  Kernels captured only
-# on small cases (their tensors stay in L2) or changed since their capture are absent.
-NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64}
+# DRAM bytes per RHS of one application of a kernel family (all its launches), measured
+# by ncu (dram__bytes.sum.per_second x duration) on captures at the bench shape (64 RHS x
+# 576^2, tensors larger than the 129 MB L2): the matvec (one launch, 298.3 MB) and the
+# three fused inverted bottlenecks (297.7 + 125.9 + 43.4 MB).  Kernels captured only on
+# small cases (their tensors stay in L2) or changed since their capture are absent.
+NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64, "k_ib_fused": 467.03e6 / 64}
 
 
 def _net_layer_bytes(I: int, B: int):
