@@ -38,8 +38,12 @@ namespace cg = cooperative_groups;
 namespace {
 
 // ---- residual + restriction ---------------------------------------------------------
-constexpr int RC_TW = 32, RC_TH = 8;                        // coarse tile
-constexpr int RF_W = 2 * RC_TW + 4, RF_H = 2 * RC_TH + 4;   // fine halo tile (68 x 20)
+// The fine halo tile is 64 complex values wide (two full warps of lanes per row), so
+// the coarse tile is 30 wide; the block is 32 x 8 threads and every pass walks rows
+// with whole warps.
+constexpr int RC_TW = 30, RC_TH = 8;                        // coarse tile
+constexpr int RF_W = 2 * RC_TW + 4, RF_H = 2 * RC_TH + 4;   // fine halo tile (64 x 20)
+static_assert(RF_W == 64, "two warp widths per tile row");
 
 __global__ void __launch_bounds__(256) k_resid_restrict(const __grid_constant__ CUtensorMap mr,
                                                         const float2* __restrict__ dinv, float2* __restrict__ rc,
@@ -53,6 +57,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const __grid_constant__ 
   __shared__ alignas(8) uint64_t bar;
   const int xc0 = blockIdx.x * RC_TW, yc0 = blockIdx.y * RC_TH;
   const int gx0 = 2 * xc0 - 2, gy0 = 2 * yc0 - 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -64,40 +69,55 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const __grid_constant__ 
   }
   if (!mbar_wait_bounded(&bar, 0, HELM_DEVERR_TMA_WAIT)) return;
   const float s = rscale ? rscale[b] : 1.f;
-  for (int i = threadIdx.x; i < RF_H * RF_W; i += blockDim.x) {
-    const int ly = i / RF_W, lx = i % RF_W;
-    const int gy = gy0 + ly, gx = gx0 + lx;
-    float2 rv = cscale(R[i], s);
-    R[i] = rv;
-    U[i] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? cmul(dinv[static_cast<long>(gy) * nx + gx], rv)
-                                                      : make_float2(0.f, 0.f);
+  // pass 1: u = dinv r on the halo tile (warp = row, lanes = columns)
+  for (int ly = ty; ly < RF_H; ly += 8) {
+    const int gy = gy0 + ly;
+    const bool rowin = gy >= 0 && gy < ny;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int lx = tx + 32 * h, gx = gx0 + lx;
+      const int i = ly * RF_W + lx;
+      float2 rv = R[i];
+      if (rscale) {
+        rv = cscale(rv, s);
+        R[i] = rv;
+      }
+      U[i] = (rowin && gx >= 0 && gx < nx) ? cmul(dinv[gy * nx + gx], rv) : make_float2(0.f, 0.f);
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < RF_H * RF_W; i += blockDim.x) {
-    const int ly = i / RF_W, lx = i % RF_W;
-    if (ly < 1 || ly > RF_H - 2 || lx < 1 || lx > RF_W - 2) continue;
-    const int gy = gy0 + ly, gx = gx0 + lx;
-    float2 q = make_float2(0.f, 0.f);
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx)
-      q = cadd(cscale(R[i], onemw), cadd(cadd(U[i - RF_W], U[i + RF_W]), cadd(U[i - 1], U[i + 1])));
-    Q[i] = q;
+  // pass 2: q = r - M u = (1 - omega) r + sum of the neighbours' u, inner rows/columns
+  for (int ly = 1 + ty; ly < RF_H - 1; ly += 8) {
+    const int gy = gy0 + ly;
+    const bool rowin = gy >= 0 && gy < ny;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int lx = tx + 32 * h, gx = gx0 + lx;
+      if (lx < 1 || lx > RF_W - 2) continue;
+      const int i = ly * RF_W + lx;
+      float2 q = make_float2(0.f, 0.f);
+      if (rowin && gx >= 0 && gx < nx)
+        q = cadd(cscale(R[i], onemw), cadd(cadd(U[i - RF_W], U[i + RF_W]), cadd(U[i - 1], U[i + 1])));
+      Q[i] = q;
+    }
   }
   __syncthreads();
-  const int cy = threadIdx.x / RC_TW, cx = threadIdx.x % RC_TW;
+  // pass 3: full-weighting restriction, one coarse point per thread
+  const int cy = ty, cx = tx;
   const int J = yc0 + cy, K = xc0 + cx;
   const int ncx = nx / 2, ncy = ny / 2;
-  if (J < ncy && K < ncx) {
+  if (cx < RC_TW && J < ncy && K < ncx) {
     const int fy = 2 * cy + 2, fx = 2 * cx + 2;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = -1; a <= 1; ++a)
+    for (int a2 = -1; a2 <= 1; ++a2)
 #pragma unroll
       for (int c = -1; c <= 1; ++c) {
-        const float w = (a == 0 ? 2.f : 1.f) * (c == 0 ? 2.f : 1.f);
-        acc = cadd(acc, cscale(Q[(fy + a) * RF_W + fx + c], w));
+        const float w = (a2 == 0 ? 2.f : 1.f) * (c == 0 ? 2.f : 1.f);
+        acc = cadd(acc, cscale(Q[(fy + a2) * RF_W + fx + c], w));
       }
     // 4 * (1/16) * sum
-    rc[static_cast<long>(b) * ncx * ncy + static_cast<long>(J) * ncx + K] = cscale(acc, 0.25f);
+    rc[static_cast<long>(b) * ncx * ncy + J * ncx + K] = cscale(acc, 0.25f);
   }
 }
 
