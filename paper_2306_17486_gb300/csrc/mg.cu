@@ -161,16 +161,16 @@ __global__ void __launch_bounds__(256) k_prolong_smooth(const __grid_constant__ 
     float2 u = make_float2(0.f, 0.f);
     if (lx >= 1 && lx <= PR_W - 2 && gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
       // bilinear prolongation I_H^h at fine (gy, gx): weights 1 at even, 1/2,1/2 at odd
+      // branch-free: the parities of (gy, gx) alternate between neighbouring lanes
       const int jy = (gy >> 1) - ey0, jx = (gx >> 1) - ex0;
       const int oy = gy & 1, ox = gx & 1;
       const float2* e0 = E + jy * PE_W + jx;
-      float2 row0 = ox ? cscale(cadd(e0[0], e0[1]), 0.5f) : e0[0];
-      float2 pe = row0;
-      if (oy) {
-        const float2* e1 = e0 + PE_W;
-        float2 row1 = ox ? cscale(cadd(e1[0], e1[1]), 0.5f) : e1[0];
-        pe = cscale(cadd(row0, row1), 0.5f);
-      }
+      const float2* e1 = oy ? e0 + PE_W : e0;          // the second coarse row only when odd
+      const float ax = ox ? 0.5f : 1.f, bx = ox ? 0.5f : 0.f;
+      const float ay = oy ? 0.5f : 1.f, by = oy ? 0.5f : 0.f;
+      const float2 r0 = cadd(cscale(e0[0], ax), cscale(e0[ox], bx));
+      const float2 r1 = cadd(cscale(e1[0], ax), cscale(e1[ox], bx));
+      const float2 pe = cadd(cscale(r0, ay), cscale(r1, by));
       u = cadd(cmul(dinv[static_cast<long>(gy) * nx + gx], rv), pe);
     }
     U[i] = u;
