@@ -265,8 +265,32 @@ __device__ __forceinline__ int twiddle_step(int e, int d, int n) {
   return e >= n ? e - n : e;
 }
 
-__device__ void dft_pad_forward(const float2* X, float2* R, float2* F, const float2* Wt, int m) {
+// The 2m x 2m DFT of the zero-padded input, the product with G_hat and the inverse DFT
+// cropped to the top-left m x m block, with the column stages done in chunks of `cw`
+// columns so that only a 2m x cw block of the spectrum is held at a time:
+//   rows    R[r][u] = sum_c X[r][c] W^(u c)                (r < m: the zero half skipped)
+//   chunk   F[v][u] = G_hat[v][u] sum_r R[r][u] W^(v r),    u in the chunk
+//           R[r][u] = sum_v F[v][u] W^(-v r)                (r < m: the discarded half skipped)
+//   rows    Y[r][c] = (1 / (2m)^2) sum_u R[r][u] W^(-u c)  (c < m)
+// The twiddle index of each term is advanced incrementally.
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat,
+                                                  int conj_g, TOut* __restrict__ y, int accumulate, int cw) {
+  const int b = blockIdx.y, k = blockIdx.x;
   const int n = 2 * m;
+  extern __shared__ float2 ism[];
+  float2* Wt = ism;               // n: W^e = exp(-2 pi i e / n)
+  float2* X = Wt + n;             // m*m   (input, later output)
+  float2* R = X + m * m;          // m*n
+  float2* F = R + m * n;          // n*cw  (one column chunk of the spectrum)
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    float s, c;
+    sincospif(-2.f * e / n, &s, &c);
+    Wt[e] = make_float2(c, s);
+  }
+  const long base = static_cast<long>(b) * m * m;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) X[i] = load_pair<TIn>(x, base + i, C, k);
+  __syncthreads();
   for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
     const int r = i / n, u = i % n;
     float2 acc = make_float2(0.f, 0.f);
@@ -278,34 +302,35 @@ __device__ void dft_pad_forward(const float2* X, float2* R, float2* F, const flo
     R[i] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int v = i / n, u = i % n;
-    float2 acc = make_float2(0.f, 0.f);
-    int e = 0;
-    for (int r = 0; r < m; ++r) {
-      acc = cadd(acc, cmul(R[r * n + u], Wt[e]));
-      e = twiddle_step(e, v, n);
+  const float2* G = ghat + static_cast<long>(k) * n * n;
+  for (int u0 = 0; u0 < n; u0 += cw) {
+    const int w = min(cw, n - u0);
+    for (int i = threadIdx.x; i < n * w; i += blockDim.x) {
+      const int v = i / w, uu = i % w;
+      float2 acc = make_float2(0.f, 0.f);
+      int e = 0;
+      for (int r = 0; r < m; ++r) {
+        acc = cadd(acc, cmul(R[r * n + u0 + uu], Wt[e]));
+        e = twiddle_step(e, v, n);
+      }
+      float2 g = G[v * n + u0 + uu];
+      if (conj_g) g.y = -g.y;
+      F[v * cw + uu] = cmul(acc, g);
     }
-    F[i] = acc;
-  }
-  __syncthreads();
-}
-
-// inverse DFT of F (2m x 2m) keeping the top-left m x m block, scaled by 1/(2m)^2
-__device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const float2* Wt, int m) {
-  const int n = 2 * m;
-  for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
-    const int r = i / n, u = i % n;
-    float2 acc = make_float2(0.f, 0.f);
-    int e = 0;
-    for (int v = 0; v < n; ++v) {
-      const float2 t = Wt[e];
-      acc = cadd(acc, cmul(F[v * n + u], make_float2(t.x, -t.y)));
-      e = twiddle_step(e, r, n);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m * w; i += blockDim.x) {
+      const int r = i / w, uu = i % w;
+      float2 acc = make_float2(0.f, 0.f);
+      int e = 0;
+      for (int v = 0; v < n; ++v) {
+        const float2 t = Wt[e];
+        acc = cadd(acc, cmul(F[v * cw + uu], make_float2(t.x, -t.y)));
+        e = twiddle_step(e, r, n);
+      }
+      R[r * n + u0 + uu] = acc;   // this chunk's columns of R are no longer needed forward
     }
-    R[i] = acc;
+    __syncthreads();
   }
-  __syncthreads();
   const float sc = 1.f / static_cast<float>(n * n);
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
     const int r = i / m, c = i % m;
@@ -316,38 +341,9 @@ __device__ void dft_crop_inverse(const float2* F, float2* R, float2* Y, const fl
       acc = cadd(acc, cmul(R[r * n + u], make_float2(t.x, -t.y)));
       e = twiddle_step(e, c, n);
     }
-    Y[i] = cscale(acc, sc);
+    X[i] = cscale(acc, sc);
   }
   __syncthreads();
-}
-
-template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat, int conj_g,
-                           TOut* __restrict__ y, int accumulate) {
-  const int b = blockIdx.y, k = blockIdx.x;
-  const int n = 2 * m;
-  extern __shared__ float2 ism[];
-  float2* Wt = ism;               // n
-  float2* X = Wt + n;             // m*m   (input, later output)
-  float2* R = X + m * m;          // m*n   scratch
-  float2* F = R + m * n;          // n*n
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    float s, c;
-    sincospif(-2.f * e / n, &s, &c);
-    Wt[e] = make_float2(c, s);
-  }
-  const long base = static_cast<long>(b) * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) X[i] = load_pair<TIn>(x, base + i, C, k);
-  __syncthreads();
-  dft_pad_forward(X, R, F, Wt, m);
-  const float2* G = ghat + static_cast<long>(k) * n * n;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    float2 g = G[i];
-    if (conj_g) g.y = -g.y;
-    F[i] = cmul(F[i], g);
-  }
-  __syncthreads();
-  dft_crop_inverse(F, R, X, Wt, m);
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
     const long idx = (base + i) * C;
     if constexpr (sizeof(TOut) == 2) {
@@ -363,6 +359,20 @@ __global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int
       }
     }
   }
+}
+
+// shared memory of k_implicit with column chunks of width cw
+static size_t implicit_chunk_smem(int m, int cw) {
+  return static_cast<size_t>(2 * m + m * m + m * 2 * m + 2 * m * cw) * sizeof(float2);
+}
+// the widest chunk (in equal parts of the 2m columns) that fits 200 KB, or 0
+static int implicit_chunk(int m) {
+  const int n = 2 * m;
+  for (int parts = 1; parts <= n; ++parts) {
+    const int cw = (n + parts - 1) / parts;
+    if (implicit_chunk_smem(m, cw) <= 200 * 1024) return cw;
+  }
+  return 0;
 }
 
 // ---- Green's function of a learned 3x3 kernel (Eq. 15), one CTA per channel ---------
@@ -567,8 +577,8 @@ int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const f
 size_t implicit_smem(int m) { return static_cast<size_t>(2 * m + m * m + m * 2 * m + 4 * m * m) * sizeof(float2); }
 
 int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat, bf16* y, cudaStream_t st) {
-  const size_t sm = implicit_smem(m);
-  if (sm > 200 * 1024) {
+  const int cw = implicit_chunk(m);
+  if (!cw) {
     set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
     return HELM_ESHAPE;
   }
@@ -577,19 +587,27 @@ int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat,
     HELM_CUDA(cudaFuncSetAttribute(k_implicit<bf16, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  HELM_LAUNCH("k_implicit", st, k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, sm, st>>>(x, m, C, ghat, 0, y, 0));
+  HELM_LAUNCH("k_implicit", st,
+              k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(x, m, C, ghat, 0, y, 0,
+                                                                                             cw));
   HELM_CHECK_LAUNCH("k_implicit");
   return HELM_OK;
 }
 
 int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* ghat, float* gx, cudaStream_t st) {
-  const size_t sm = implicit_smem(m);
+  const int cw = implicit_chunk(m);
+  if (!cw) {
+    set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
+    return HELM_ESHAPE;
+  }
   static bool attr = false;
   if (!attr) {
     HELM_CUDA(cudaFuncSetAttribute(k_implicit<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  HELM_LAUNCH("k_implicit_adj", st, k_implicit<float, float><<<dim3(C / 2, B), 256, sm, st>>>(gy, m, C, ghat, 1, gx, 1));
+  HELM_LAUNCH("k_implicit_adj", st,
+              k_implicit<float, float><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(gy, m, C, ghat, 1, gx, 1,
+                                                                                               cw));
   HELM_CHECK_LAUNCH("k_implicit_adj");
   return HELM_OK;
 }

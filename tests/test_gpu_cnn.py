@@ -62,7 +62,7 @@ def test_green_function_matches_oracle(helm, m):
     assert err < 2e-5, err
 
 
-@pytest.mark.parametrize("I,skip_threshold,B", [(64, 512, 2), (128, 64, 2), (96, 512, 1)])
+@pytest.mark.parametrize("I,skip_threshold,B", [(64, 512, 2), (128, 64, 2), (96, 512, 1), (576, 2048, 1)])
 def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
     P, running = _random_net(5)
     # the GPU's conv weights are BF16: give the oracle the same rounded values
@@ -84,9 +84,11 @@ def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
     for i in range(B):
         err = np.linalg.norm(e[i] - ref[i]) / np.linalg.norm(ref[i])
         assert err < 4e-2, (i, err)
-    # scale equivariance holds exactly up to rounding: e(3r) = 3 e(r)
+    # scale equivariance holds up to rounding: e(3r) = 3 e(r).  r / s differs from
+    # 3r / 3s in the last FP32 digit, which can flip the BF16 rounding of a few
+    # activations on a large grid: bound one BF16 ulp (2^-8) of the output norm
     e3 = net.apply(p, torch.tensor(3 * r, dtype=torch.complex64, device="cuda")).cpu().numpy()
-    assert np.linalg.norm(e3 - 3 * e) <= 1e-5 * np.linalg.norm(3 * e)
+    assert np.linalg.norm(e3 - 3 * e) <= 2.0 ** -8 * np.linalg.norm(3 * e)
 
 
 def test_composed_preconditioner_matches_oracle(helm):
