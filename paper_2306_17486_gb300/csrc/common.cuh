@@ -153,4 +153,22 @@ int make_c64_map(CUtensorMap* out, const void* base, int nx, int ny, int nb, int
 
 inline int div_up(long a, long b) { return static_cast<int>((a + b - 1) / b); }
 
+// Multiprocessor count of the current device (cached per device).
+int sm_count(int* out);
+
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device, once
+// per device: `done` is the caller's bitmask of devices already configured (the
+// attribute belongs to a device, so a process using several GPUs sets it on each).
+template <class K>
+inline int smem_attr_once(K* kernel, int bytes, unsigned long long* done) {
+  int dev = 0;
+  HELM_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(*done & bit)) {
+    HELM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    *done |= bit;
+  }
+  return HELM_OK;
+}
+
 }  // namespace helm

@@ -410,16 +410,11 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     helm::set_error("conv: shared memory %zu bytes exceeds the per-CTA limit (grid row too wide)", smem);
     return HELM_ESHAPE;
   }
-  static int nsm = 0;
-  static bool attr = false;
-  if (!attr) {
-    HELM_CUDA(cudaFuncSetAttribute(k_conv_tc<CS, COUT, TAPS, PH, MTR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   227 * 1024));
-    int dev;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    attr = true;
-  }
+  static unsigned long long attr_done = 0;
+  int rc = helm::smem_attr_once(k_conv_tc<CS, COUT, TAPS, PH, MTR>, 227 * 1024, &attr_done);
+  int nsm = 0;
+  if (!rc) rc = helm::sm_count(&nsm);
+  if (rc) return rc;
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA), TMEM
   // columns (512 per SM) and registers (at most two 288-thread CTAs below 113 registers)
   int per_sm = static_cast<int>((228 * 1024) / (smem + 1024));

@@ -309,16 +309,11 @@ int launch_ib_t(const IbArgs& a0, cudaStream_t st) {
   a.tiles_x = helm::div_up(a.W, IB_TW);
   a.tiles_y = helm::div_up(a.H, IB_TH);
   a.ntiles = a.tiles_x * a.tiles_y * a.B;
-  static int nsm = 0;
-  static bool attr = false;
-  if (!attr) {
-    HELM_CUDA(cudaFuncSetAttribute(k_ib_fused<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(Cfg::SMEM)));
-    int dev;
-    HELM_CUDA(cudaGetDevice(&dev));
-    HELM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    attr = true;
-  }
+  static unsigned long long attr_done = 0;
+  int rc = helm::smem_attr_once(k_ib_fused<C>, static_cast<int>(Cfg::SMEM), &attr_done);
+  int nsm = 0;
+  if (!rc) rc = helm::sm_count(&nsm);
+  if (rc) return rc;
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA) and TMEM
   const int per_sm = std::max(1, std::min(static_cast<int>((228 * 1024) / (Cfg::SMEM + 1024)), 2));
   const int grid = std::max(1, std::min(a.ntiles, nsm * per_sm));

@@ -45,6 +45,16 @@ static PFN_encodeTiled get_encode() {
   return fn;
 }
 
+int sm_count(int* out) {
+  static int cache[64] = {};
+  int dev = 0;
+  HELM_CUDA(cudaGetDevice(&dev));
+  int& c = cache[dev & 63];
+  if (!c) HELM_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev));
+  *out = c;
+  return HELM_OK;
+}
+
 int make_c64_map(CUtensorMap* out, const void* base, int nx, int ny, int nb, int box_w, int box_h) {
   PFN_encodeTiled enc = get_encode();
   if (!enc) {
