@@ -31,7 +31,10 @@ def _worker(rank, world, port, out):
 def test_two_ranks_disjoint_work_and_max_time():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29500 + os.getpid() % 1000
+    import socket
+    with socket.socket() as sk:   # a port the OS reports free on 127.0.0.1
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
