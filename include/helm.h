@@ -228,6 +228,9 @@ typedef struct {
   int expansion;      /* inverted-bottleneck expansion factor (6)                         */
   int skip_threshold; /* grids below this size keep the coarsest level at I/8 (512)       */
   int literal_green;  /* 0: Eq. (15) read as conj(K)/(|K|^2+eps); 1: literal K/(K^2+eps) */
+  int explicit_unet;  /* 0: the implicit U-Net (Section 4.2); 1: the explicit U-Net that
+                         Section 6 compares it with, the same network without the implicit
+                         step at the coarsest level (no "s.imp.K" parameter, no G_hat)     */
 } helm_cnn_desc;
 
 /* Create a network (all parameters owned by the caller, see helm_cnn_set_params); the
@@ -298,7 +301,7 @@ int helm_adam_step(float* params, const float* grads, float* m, float* v, long n
                    double beta2, double eps, int step, void* stream);
 
 /* Copy G_hat (Eq. 15, after crop and DFT) for coarsest size m to out_dev, complex64
- * [nk][2m][2m]; builds it if needed. */
+ * [nk][2m][2m]; builds it if needed.  HELM_ESTATE for an explicit U-Net. */
 int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream);
 
 /* The composed preconditioner of Section 4.1: z = e + V(r - A e), e = s Net(r/s), s = RMS(r). */

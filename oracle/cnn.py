@@ -25,6 +25,8 @@ Architecture (c0 = 16, expansion t = 6; readings where the paper is silent):
     3x3 depthwise + BN + softplus, 1x1 project tc->c + BN, identity skip.
   No conv bias where BN follows.  BN eps 1e-5, momentum 0.1; softplus beta = 1.
   Implicit kernels initialised to L + iI (Section 5.3).
+  Explicit U-Net (Section 6, the comparison network): the same encoder-solver network
+  without the implicit step at the coarsest level (implicit=False below).
 """
 from __future__ import annotations
 
@@ -65,8 +67,9 @@ def _ib(spec, name, c, t):
     _bn(spec, name + ".bn2", c)
 
 
-def param_spec(c0: int = 16, t: int = 6):
-    """Ordered list of (name, shape, fan_in, kind[, values]) for every learnable tensor."""
+def param_spec(c0: int = 16, t: int = 6, implicit: bool = True):
+    """Ordered list of (name, shape, fan_in, kind[, values]) for every learnable tensor
+    (implicit=False: the explicit U-Net, which has no implicit kernels)."""
     C = [c0, 2 * c0, 4 * c0]
     spec = []
     cin = 2
@@ -86,10 +89,11 @@ def param_spec(c0: int = 16, t: int = 6):
     for j in range(3):                       # level 4 downsampling module
         _conv(spec, f"s.l4.conv{j}", C[2], C[2])
         _bn(spec, f"s.l4.bn{j}", C[2])
-    nk = C[2] // 2                           # implicit layer: complex kernels
-    K0 = imp.laplacian_plus_i()
-    init = np.stack([np.broadcast_to(K0.real, (nk, 3, 3)), np.broadcast_to(K0.imag, (nk, 3, 3))])
-    spec.append(("s.imp.K", (2, nk, 3, 3), 0, "fixed", init.ravel()))
+    if implicit:
+        nk = C[2] // 2                       # implicit layer: complex kernels
+        K0 = imp.laplacian_plus_i()
+        init = np.stack([np.broadcast_to(K0.real, (nk, 3, 3)), np.broadcast_to(K0.imag, (nk, 3, 3))])
+        spec.append(("s.imp.K", (2, nk, 3, 3), 0, "fixed", init.ravel()))
     ups = [(C[2], C[2]), (C[2], C[1]), (C[1], C[0])]
     for k, (ci, co) in enumerate(ups):
         _convT(spec, f"s.up{k+1}.convT", ci, co)
@@ -115,8 +119,8 @@ def init_running(c0: int = 16, t: int = 6):
     return {n: (np.zeros(c), np.ones(c)) for n, c in bn_names(c0, t)}
 
 
-def num_params(c0: int = 16, t: int = 6) -> int:
-    return int(sum(np.prod(s) for _, s, *_ in param_spec(c0, t)))
+def num_params(c0: int = 16, t: int = 6, implicit: bool = True) -> int:
+    return int(sum(np.prod(s) for _, s, *_ in param_spec(c0, t, implicit)))
 
 
 # ----------------------------------------------------------------------------------
@@ -385,7 +389,8 @@ def encoder(tp, kfeat: Var, train, running):
 
 
 def solver(tp, x0: Var, encs, ghat, train, running, skip: bool):
-    """x0 [B, 2, I/2, I/2] (restricted, normalised residual) -> p [B, 2, I/2, I/2]."""
+    """x0 [B, 2, I/2, I/2] (restricted, normalised residual) -> p [B, 2, I/2, I/2];
+    ghat None: the explicit U-Net (no implicit step)."""
     feats = []
     x = x0
     for k in range(3):
@@ -397,7 +402,8 @@ def solver(tp, x0: Var, encs, ghat, train, running, skip: bool):
     x = conv_bn_act(tp, x, "s.l4.conv0", "s.l4.bn0", 1 if skip else 2, train, running)
     x = conv_bn_act(tp, x, "s.l4.conv1", "s.l4.bn1", 1, train, running)
     x = conv_bn_act(tp, x, "s.l4.conv2", "s.l4.bn2", 1, train, running)
-    x = implicit_layer(tp, x, "s.imp.K", ghat)
+    if ghat is not None:
+        x = implicit_layer(tp, x, "s.imp.K", ghat)
     for k in range(3):
         p = f"s.up{k+1}"
         st = 1 if (k == 0 and skip) else 2
@@ -416,11 +422,14 @@ def kappa_features(kappa: np.ndarray, gamma: np.ndarray) -> np.ndarray:
 
 class Network:
     """Encoder-solver network with parameters `params` (dict name -> float64 array)
-    and BatchNorm running statistics `running` (dict bn name -> (mean, var))."""
+    and BatchNorm running statistics `running` (dict bn name -> (mean, var));
+    implicit=False is the explicit U-Net of Section 6."""
 
-    def __init__(self, params, running=None, c0: int = 16, t: int = 6, literal_green=False):
+    def __init__(self, params, running=None, c0: int = 16, t: int = 6, literal_green=False,
+                 implicit: bool = True):
         self.params = params
         self.c0, self.t = c0, t
+        self.implicit = implicit
         self.running = init_running(c0, t) if running is None else running
         self.literal_green = literal_green
         self._ghat = {}
@@ -450,7 +459,7 @@ class Network:
         kf = Var(kfeat)
         encs = encoder(tp, kf, train, running)
         m = coarsest_size(I, skip)
-        p = solver(tp, x0, encs, self.ghat(m), train, running, skip)
+        p = solver(tp, x0, encs, self.ghat(m) if self.implicit else None, train, running, skip)
         pc = p.a[:, 0] + 1j * p.a[:, 1]
         e = prolong(pc) * s[:, None, None]
         tp.out = p

@@ -209,11 +209,16 @@ def conv_bf16(x: torch.Tensor, w: torch.Tensor, mode: str = "s1", scale=None, sh
 
 class Cnn:
     """The encoder-solver network: FP32 parameters (`params`, a flat CUDA tensor in the
-    library's parameter order) and BN running statistics live on the device."""
+    library's parameter order) and BN running statistics live on the device.
+    explicit_unet=True gives the explicit U-Net of Section 6: the same network without
+    the implicit step at the coarsest level."""
 
-    def __init__(self, c0=16, expansion=6, skip_threshold=512, literal_green=False, device="cuda"):
+    def __init__(self, c0=16, expansion=6, skip_threshold=512, literal_green=False, explicit_unet=False,
+                 device="cuda"):
         d = _lib.CnnDesc()
         d.c0, d.expansion, d.skip_threshold, d.literal_green = c0, expansion, skip_threshold, int(literal_green)
+        d.explicit_unet = int(explicit_unet)
+        self.explicit_unet = bool(explicit_unet)
         h = C.c_void_p()
         check(lib().helm_cnn_create(C.byref(d), C.byref(h)), "helm_cnn_create")
         self.handle = h
@@ -298,7 +303,8 @@ class Cnn:
         check(lib().helm_cnn_set_running(self.handle, _ptr(self.running), _stream()), "set_running")
 
     def ghat(self, m: int) -> torch.Tensor:
-        nk = dict((n, s) for n, s, _ in self.spec)["s.imp.K"][1]
+        shapes = dict((n, s) for n, s, _ in self.spec)
+        nk = shapes["s.imp.K"][1] if "s.imp.K" in shapes else 1   # explicit U-Net: the call fails
         out = torch.empty((nk, 2 * m, 2 * m), dtype=torch.complex64, device=self.device)
         check(lib().helm_cnn_get_ghat(self.handle, m, _ptr(out), _stream()), "get_ghat")
         return out

@@ -34,7 +34,8 @@ class FgmresStats(C.Structure):
 
 
 class CnnDesc(C.Structure):
-    _fields_ = [("c0", i32), ("expansion", i32), ("skip_threshold", i32), ("literal_green", i32)]
+    _fields_ = [("c0", i32), ("expansion", i32), ("skip_threshold", i32), ("literal_green", i32),
+                ("explicit_unet", i32)]
 
 
 # name -> (restype, argtypes)

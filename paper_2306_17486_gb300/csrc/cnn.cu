@@ -68,7 +68,7 @@ void build_params(helm_cnn* c) {
     add_param(c, "s.l4.conv" + std::to_string(j) + ".w", {C[2], C[2], 3, 3});
     add_bn(c, "s.l4.bn" + std::to_string(j), C[2]);
   }
-  add_param(c, "s.imp.K", {2, C[2] / 2, 3, 3});
+  if (!c->desc.explicit_unet) add_param(c, "s.imp.K", {2, C[2] / 2, 3, 3});
   const int ups[3][2] = {{C[2], C[2]}, {C[2], C[1]}, {C[1], C[0]}};
   for (int k = 0; k < 3; ++k) {
     const std::string p = "s.up" + std::to_string(k + 1);
@@ -210,17 +210,20 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
   pl->layers.push_back(conv_layer(c, "s.l4.conv0.w", "s.l4.bn0", skip ? HELM_CONV_S1 : HELM_CONV_S2, x, l4a, -1, -1));
   pl->layers.push_back(conv_layer(c, "s.l4.conv1.w", "s.l4.bn1", HELM_CONV_S1, l4a, l4b, -1, -1));
   pl->layers.push_back(conv_layer(c, "s.l4.conv2.w", "s.l4.bn2", HELM_CONV_S1, l4b, l4c, -1, -1));
-  const int imp = pl->add_tensor(B, m, m, C[2]);
-  Layer li{};
-  li.kind = L_IMPL;
-  li.wparam = c->pidx.at("s.imp.K");
-  li.bn = -1;
-  li.ci = li.co = C[2];
-  li.in = l4c;
-  li.out = imp;
-  li.add1 = li.add2 = -1;
-  pl->layers.push_back(li);
-  x = imp;
+  x = l4c;
+  if (!c->desc.explicit_unet) {
+    const int imp = pl->add_tensor(B, m, m, C[2]);
+    Layer li{};
+    li.kind = L_IMPL;
+    li.wparam = c->pidx.at("s.imp.K");
+    li.bn = -1;
+    li.ci = li.co = C[2];
+    li.in = l4c;
+    li.out = imp;
+    li.add1 = li.add2 = -1;
+    pl->layers.push_back(li);
+    x = imp;
+  }
   const int upc[3] = {C[2], C[1], C[0]};
   int Hu = m;
   for (int k = 0; k < 3; ++k) {
@@ -296,7 +299,7 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
     c->ghat.clear();
     c->dirty = false;
   }
-  if (m > 0 && !c->ghat.count(m)) {
+  if (m > 0 && !c->desc.explicit_unet && !c->ghat.count(m)) {
     const ParamInfo& K = c->params[c->pidx.at("s.imp.K")];
     const int nk = K.shape[1];
     const size_t need = greens_scratch_elems(m, nk);
@@ -512,10 +515,14 @@ int helm_cnn_create(const helm_cnn_desc* desc, helm_cnn** out) {
     set_error("helm_cnn_create: null output");
     return HELM_EINVAL;
   }
-  helm_cnn_desc d = {16, 6, 512, 0};
+  helm_cnn_desc d = {16, 6, 512, 0, 0};
   if (desc) d = *desc;
   if (d.c0 != 16 || d.expansion != 6) {
     set_error("helm_cnn_create: kernels are instantiated for c0 = 16, expansion = 6");
+    return HELM_EINVAL;
+  }
+  if (d.explicit_unet != 0 && d.explicit_unet != 1) {
+    set_error("helm_cnn_create: explicit_unet must be 0 or 1");
     return HELM_EINVAL;
   }
   helm_cnn* c = new helm_cnn();
@@ -662,6 +669,10 @@ int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream) {
   if (!c || m <= 0 || !out_dev) {
     helm::set_error("helm_cnn_get_ghat: invalid argument");
     return HELM_EINVAL;
+  }
+  if (c->desc.explicit_unet) {
+    helm::set_error("helm_cnn_get_ghat: the explicit U-Net has no implicit layer");
+    return HELM_ESTATE;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = helm::cnn_derive(c, m, st);

@@ -246,11 +246,12 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--init", default=None, help="start from these weights (fine-tuning)")
+    ap.add_argument("--explicit", action="store_true", help="the explicit U-Net (no implicit step, Section 6)")
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import synth
-    net = Cnn(skip_threshold=a.skip_threshold)
+    net = Cnn(skip_threshold=a.skip_threshold, explicit_unet=a.explicit)
     prev = {}
     if a.init:
         prev = load_weights(net, a.init)
@@ -265,6 +266,7 @@ def main():
     dt = time.time() - t0
     meta = {"steps": a.steps + int(prev.get("steps") or 0), "batch": a.batch, "sizes": a.sizes,
             "pattern": a.pattern, "seed": a.seed, "lr": a.lr, "skip_threshold": a.skip_threshold,
+            "explicit_unet": bool(a.explicit),
             "seconds": dt + float(prev.get("seconds") or 0.0), "history": [list(h) for h in hist]}
     if a.init:
         meta["init"] = {k: prev.get(k) for k in ("steps", "sizes", "seconds")}

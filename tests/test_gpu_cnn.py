@@ -34,11 +34,12 @@ def _bf(a):
     return torch.tensor(np.asarray(a), dtype=torch.float32).to(torch.bfloat16).double().numpy()
 
 
-def _random_net(seed):
-    P = synth.random_params(ocnn.param_spec(16), seed=seed, bn_jitter=0.2)
+def _random_net(seed, implicit=True):
+    P = synth.random_params(ocnn.param_spec(16, implicit=implicit), seed=seed, bn_jitter=0.2)
     rng = np.random.default_rng(seed + 1)
-    K = P["s.imp.K"]
-    P["s.imp.K"] = K + 0.1 * rng.standard_normal(K.shape)
+    if implicit:
+        K = P["s.imp.K"]
+        P["s.imp.K"] = K + 0.1 * rng.standard_normal(K.shape)
     running = {n: (0.1 * rng.standard_normal(c), rng.uniform(0.5, 2.0, c)) for n, c in ocnn.bn_names(16)}
     return P, running
 
@@ -49,6 +50,17 @@ def test_parameter_table_matches_oracle(helm):
     assert [(n, tuple(s)) for n, s, *_ in spec] == [(n, s) for n, s, _ in net.spec]
     assert [n for n, _ in ocnn.bn_names(16)] == [n for n, _, _ in net.bn]
     assert net.nparams == ocnn.num_params(16)
+
+
+def test_explicit_unet_parameter_table_matches_oracle(helm):
+    """Section 6's explicit U-Net: the same table without the implicit kernels."""
+    net = helm.Cnn(explicit_unet=True)
+    spec = ocnn.param_spec(16, implicit=False)
+    assert [(n, tuple(s)) for n, s, *_ in spec] == [(n, s) for n, s, _ in net.spec]
+    assert net.nparams == ocnn.num_params(16, implicit=False) == ocnn.num_params(16) - 576
+    assert [n for n, _ in ocnn.bn_names(16)] == [n for n, _, _ in net.bn]
+    with pytest.raises(RuntimeError):
+        net.ghat(4)
 
 
 @pytest.mark.parametrize("m", [4, 8, 16, 36])
@@ -62,12 +74,14 @@ def test_green_function_matches_oracle(helm, m):
     assert err < 2e-5, err
 
 
-@pytest.mark.parametrize("I,skip_threshold,B", [(64, 512, 2), (128, 64, 2), (96, 512, 1), (576, 2048, 1)])
-def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
-    P, running = _random_net(5)
+@pytest.mark.parametrize("I,skip_threshold,B,explicit", [(64, 512, 2, False), (128, 64, 2, False), (96, 512, 1, False),
+                                                          (576, 2048, 1, False), (64, 512, 2, True),
+                                                          (128, 64, 2, True)])
+def test_network_forward_matches_oracle(helm, I, skip_threshold, B, explicit):
+    P, running = _random_net(5, implicit=not explicit)
     # the GPU's conv weights are BF16: give the oracle the same rounded values
     Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
-    net = helm.Cnn(skip_threshold=skip_threshold)
+    net = helm.Cnn(skip_threshold=skip_threshold, explicit_unet=explicit)
     net.load_dict(Pq)
     net.load_running(running)
     abl = I // 8
@@ -78,7 +92,7 @@ def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
     r = synth.random_complex((B, I, I), 9).astype(np.complex64).astype(np.complex128)
     e = net.apply(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
     op = ohz.Problem(kappa, abl, omega_h=oh)
-    on = ocnn.Network(Pq, running, c0=16)
+    on = ocnn.Network(Pq, running, c0=16, implicit=not explicit)
     ref, _ = on.forward(r, ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64)),
                         train=False, skip=I < skip_threshold)
     for i in range(B):
@@ -91,11 +105,12 @@ def test_network_forward_matches_oracle(helm, I, skip_threshold, B):
     assert np.linalg.norm(e3 - 3 * e) <= 2.0 ** -8 * np.linalg.norm(3 * e)
 
 
-def test_composed_preconditioner_matches_oracle(helm):
+@pytest.mark.parametrize("explicit", [False, True], ids=["implicit", "explicit"])
+def test_composed_preconditioner_matches_oracle(helm, explicit):
     I, abl, B = 64, 8, 2
-    P, running = _random_net(11)
+    P, running = _random_net(11, implicit=not explicit)
     Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
-    net = helm.Cnn()
+    net = helm.Cnn(explicit_unet=explicit)
     net.load_dict(Pq)
     net.load_running(running)
     kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 2).astype(np.float32).astype(np.float64)
@@ -106,7 +121,7 @@ def test_composed_preconditioner_matches_oracle(helm):
     z = net.precond(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
     op = ohz.Problem(kappa, abl, omega_h=oh)
     mg = omg.SLMultigrid(op, 3)
-    on = ocnn.Network(Pq, running, c0=16)
+    on = ocnn.Network(Pq, running, c0=16, implicit=not explicit)
     kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
     from oracle.training import composed_preconditioner
     M = composed_preconditioner(op, on, kf, mg)
@@ -116,16 +131,16 @@ def test_composed_preconditioner_matches_oracle(helm):
         assert err < 4e-2, err
 
 
-@pytest.mark.parametrize("I,skip_threshold", [(64, 512), (128, 64)])
-def test_training_forward_and_gradients_match_oracle(helm, I, skip_threshold):
+@pytest.mark.parametrize("I,skip_threshold,explicit", [(64, 512, False), (128, 64, False), (64, 512, True)])
+def test_training_forward_and_gradients_match_oracle(helm, I, skip_threshold, explicit):
     """Batch-statistics forward and every parameter gradient vs the oracle's
     hand-written reverse mode (the oracle's gradients are pinned by finite differences).
     BF16 activations in the GPU forward leave gradient errors of a few percent; per
     tensor the relative 2-norm error must stay below 10% and the cosine above 0.99."""
     B = 2
-    P, running = _random_net(21)
+    P, running = _random_net(21, implicit=not explicit)
     Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
-    net = helm.Cnn(skip_threshold=skip_threshold)
+    net = helm.Cnn(skip_threshold=skip_threshold, explicit_unet=explicit)
     net.load_dict(Pq)
     abl = I // 8
     kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 3).astype(np.float32).astype(np.float64)
@@ -141,7 +156,7 @@ def test_training_forward_and_gradients_match_oracle(helm, I, skip_threshold):
     loss, ge = helm.mse_loss(eg, torch.tensor(et, dtype=torch.complex64, device="cuda"))
     grads = net.to_dict(net.backward(p, ge))
     op = ohz.Problem(kappa, abl, omega_h=oh, gamma0=0.05)
-    on = ocnn.Network(Pq, None, c0=16)
+    on = ocnn.Network(Pq, None, c0=16, implicit=not explicit)
     kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
     from oracle.training import mse_loss as omse
     e_ref, tp = on.forward(r, kf, train=True, skip=I < skip_threshold, record=True)

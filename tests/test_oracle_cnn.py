@@ -16,9 +16,9 @@ from oracle import training as tr
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
 
 
-def _setup(I=32, B=2, c0=4, seed=1):
-    P = synth.random_params(cnn.param_spec(c0), seed=seed, bn_jitter=0.2)
-    net = cnn.Network(P, c0=c0)
+def _setup(I=32, B=2, c0=4, seed=1, implicit=True):
+    P = synth.random_params(cnn.param_spec(c0, implicit=implicit), seed=seed, bn_jitter=0.2)
+    net = cnn.Network(P, c0=c0, implicit=implicit)
     abl = 4
     prob = hz.Problem(synth.grf_kappa(I - 2 * abl, abl, 4.0, seed + 1), abl)
     kf = cnn.kappa_features(prob.kappa, prob.gamma)
@@ -27,11 +27,13 @@ def _setup(I=32, B=2, c0=4, seed=1):
     return net, P, kf, r, et
 
 
+@pytest.mark.parametrize("implicit", [True, False], ids=["implicit", "explicit"])
 @pytest.mark.parametrize("skip", [True, False])
-def test_network_gradients_match_central_differences(skip):
+def test_network_gradients_match_central_differences(skip, implicit):
     """Every parameter tensor: directional derivative of the Eq. (16) loss along a
-    random direction, analytic vs central differences (FP64), relative 1e-6."""
-    net, P, kf, r, et = _setup()
+    random direction, analytic vs central differences (FP64), relative 1e-6; for the
+    implicit U-Net and for the explicit U-Net of Section 6."""
+    net, P, kf, r, et = _setup(implicit=implicit)
 
     def loss_of(params):
         net.params = params
@@ -61,6 +63,11 @@ def test_parameter_count_and_feature_shapes_match_paper():
     n_solver = sum(int(np.prod(s)) for n, s, *_ in cnn.param_spec(16) if n.startswith("s."))
     ref = GOLD["solver_params"]["value"]
     assert abs(n_solver - ref) / ref < 0.03          # 360K (Table 4)
+    n_expl = sum(int(np.prod(s)) for n, s, *_ in cnn.param_spec(16, implicit=False) if n.startswith("s."))
+    ref_e = GOLD["explicit_solver_params"]["value"]
+    assert abs(n_expl - ref_e) / ref_e < 0.03        # 360K (Table 4, explicit model)
+    # the two differ by the 32 complex 3x3 kernels of the implicit step (Section 4.2)
+    assert n_solver - n_expl == 32 * 9 * 2
     P = synth.random_params(cnn.param_spec(16), seed=0)
     net = cnn.Network(P, c0=16)
     I = 64
@@ -73,6 +80,35 @@ def test_parameter_count_and_feature_shapes_match_paper():
     assert cnn.coarsest_size(256) == 256 // 8
     assert cnn.skip_last_down(GOLD["skip_threshold"]["value"] - 1)
     assert not cnn.skip_last_down(GOLD["skip_threshold"]["value"])
+
+
+def test_explicit_unet_is_the_implicit_one_with_an_identity_step():
+    """Section 6's explicit U-Net is the implicit network without the implicit step.
+    With G_hat = 1 the implicit step crop(IFFT(FFT(pad(x)))) is the identity, so the
+    two networks must agree on the same parameters: outputs in training and in
+    evaluation mode, and every shared parameter's gradient."""
+    net_i, P, kf, r, et = _setup(implicit=True)
+    nk = P["s.imp.K"].shape[1]
+    net_i.ghat = lambda m: np.ones((nk, 2 * m, 2 * m), dtype=np.complex128)
+    Pe = {k: v for k, v in P.items() if k != "s.imp.K"}
+    net_e = cnn.Network(Pe, c0=4, implicit=False)
+    assert set(P) - set(Pe) == {"s.imp.K"}
+    assert [n for n, *_ in cnn.param_spec(4, implicit=False)] == [n for n, *_ in cnn.param_spec(4) if n != "s.imp.K"]
+    for skip in (True, False):
+        ei, _ = net_i.forward(r, kf, train=False, skip=skip)
+        ee, _ = net_e.forward(r, kf, train=False, skip=skip)
+        assert np.abs(ee - ei).max() <= 1e-12 * np.abs(ei).max()
+        ei, ti = net_i.forward(r, kf, train=True, skip=skip, record=True)
+        ee, te = net_e.forward(r, kf, train=True, skip=skip, record=True)
+        assert np.abs(ee - ei).max() <= 1e-12 * np.abs(ei).max()
+        gi = net_i.backward(ti, tr.mse_loss(ei, et)[1])
+        ge = net_e.backward(te, tr.mse_loss(ee, et)[1])
+        assert set(ge) == set(Pe)
+        for k in Pe:
+            assert np.abs(ge[k] - gi[k]).max() <= 1e-10 * max(np.abs(gi[k]).max(), 1e-300), k
+    # the implicit step is not the identity for the real G_hat (L + iI kernels)
+    net_r = cnn.Network(P, c0=4)
+    assert np.abs(net_r.forward(r, kf)[0] - net_e.forward(r, kf)[0]).max() > 1e-3 * np.abs(ei).max()
 
 
 def test_bn_eval_folding_equivalence():
