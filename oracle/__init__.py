@@ -13,13 +13,14 @@ Modules
   multigrid  - Eq. (4), (6), (8), Algorithm 1: shifted-Laplacian V-cycle
   fgmres     - flexible GMRES (Saad 1993), right-preconditioned, restarted
   implicit   - Eq. (14), (15): implicit layer and Green's function, adjoints
-  cnn        - encoder-solver U-Net (Sections 4.1-4.4, 5.3), forward + backward
+  cnn        - encoder-solver U-Net (Sections 4.1-4.4, 5.3), forward + backward; also
+               the explicit U-Net of Section 6 (the same network without the implicit step)
   training   - Eq. (16) loss, Eq. (17) data generation, Adam
 
 Pins: every function above is checked against something other than itself (assembled
 matrices, dense LU, closed forms, LFA, finite differences, the paper's printed
 constants) by the `-m "not gpu"` tests.  Parity unpinned: the results of training and
-the iteration counts of a trained network (the paper's datasets and weights are not
-available); `training.composed_preconditioner` is pinned only as a composition of
-pinned parts.
+the iteration counts of a trained network, implicit or explicit (the paper's datasets
+and weights are not available); `training.composed_preconditioner` is pinned only as a
+composition of pinned parts.
 """
