@@ -40,6 +40,12 @@ def test_host_side_validation_without_gpu(L):
     L.helm_fgmres_opts_default(ctypes.byref(f))
     assert (f.restart, f.rtol, f.maxit, f.warmup_iters, f.reorth, f.cnn_every) == (10, 1e-6, 2000, 3, 1, 1)
     assert L.helm_version().startswith(b"helm-gb300")
+    # network descriptor checks also precede any device allocation
+    d = _lib.CnnDesc(16, 6, 512, 0, 2)                # explicit_unet must be 0 or 1
+    assert L.helm_cnn_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == -1
+    assert b"explicit_unet" in L.helm_last_error_string()
+    d = _lib.CnnDesc(8, 6, 512, 0, 0)                 # kernels exist for c0 = 16 only
+    assert L.helm_cnn_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == -1
     assert ctypes.sizeof(_lib.FgmresStats) == 24
 
 
