@@ -22,6 +22,10 @@ Conventions (readings of the paper where it is silent):
     extrapolation through that zero is -(2^l - 1) u_0, which adds 2^l - 1 to the
     diagonal of the first row and column (folded into the mass term).  Without it
     the 3-level cycle diverges at omega = 0 (spectral radius 1.18 on 32^2).
+  * Neumann and Sommerfeld problems (see oracle.helmholtz): every level is
+    rediscretised with the same boundary condition, c times the boundary sides added
+    to its mass with kappa_l = sqrt(restricted kappa^2) and h_l = 2^l h; the low-side
+    correction above belongs to the Dirichlet condition only.
   * Relaxation: damped Jacobi u <- u + w D^{-1} (r - M u), D = diag(M), w = 0.8,
     one pre- and one post-sweep (Section 3.4), zero initial guess on every level.
   * Coarsest level: either a dense LU solve, or a fixed number (10) of GMRES
@@ -33,7 +37,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg
 
-from .helmholtz import apply_stencil, sl_mass
+from .helmholtz import apply_stencil, boundary_mass, sl_mass
 
 FW = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]])
 R_KERNEL = FW / 16.0   # I_h^H, Eq. (8)
@@ -122,7 +126,8 @@ class SLMultigrid:
     coarse       : 'gmres' (Section 3.4 default) or 'lu'
     coarse_iters : GMRES iterations on the coarsest level
     sl_includes_gamma : ablation flag, shift (1 - (beta+gamma) i)
-    boundary_fix : keep the low-side Dirichlet boundary at the fine position (default)
+    boundary_fix : keep the low-side Dirichlet boundary at the fine position (default;
+                   Dirichlet problems only)
     """
 
     def __init__(self, problem, levels: int, beta: float = 0.5, omega_j: float = 0.8,
@@ -135,11 +140,14 @@ class SLMultigrid:
         self.coarse_iters = coarse_iters
         k2 = problem.kappa ** 2
         g = problem.gamma
+        bc = getattr(problem, "bc", "dirichlet")
         self.mass = []
         for l in range(levels):
             oh = problem.omega_h * (2 ** l)
             m = sl_mass(k2, oh, beta, gamma=g if sl_includes_gamma else None)
-            if boundary_fix and l > 0:
+            if bc != "dirichlet":
+                m = m + boundary_mass(np.sqrt(k2), oh, bc)
+            elif boundary_fix and l > 0:
                 m = m.copy()
                 m[0, :] -= 2 ** l - 1
                 m[:, 0] -= 2 ** l - 1
