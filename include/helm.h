@@ -64,7 +64,16 @@ extern "C" {
 
 typedef struct helm_problem helm_problem; /* one slowness model + frequency + multigrid  */
 
-/* Multigrid options (Section 3.2 / 3.4). */
+/* ---- boundary conditions outside the grid (helm_mg_opts.bc) ------------------------
+ * Each replaces the ghost value next to a boundary node u_b by c u_b, which adds c per
+ * boundary side to the node's mass term; the stencil kernels are the same for all.   */
+#define HELM_BC_DIRICHLET 0  /* c = 0: zero padding, the paper's setting (Section 3.4)       */
+#define HELM_BC_NEUMANN 1    /* c = 1: replication padding (Section 3.4, remark on Neumann)  */
+#define HELM_BC_SOMMERFELD 2 /* c = 1 - i omega h kappa_b: first-order outgoing-wave
+                                condition du/dn + i omega kappa u = 0 (Section 3.1 names
+                                Sommerfeld as an alternative to the absorbing layer)     */
+
+/* Multigrid options (Section 3.2 / 3.4); also the problem's boundary condition. */
 typedef struct {
   int levels;            /* grid levels incl. the finest (>= 2); nx, ny divisible by 2^levels */
   double beta;           /* imaginary shift of Eq. (4), alpha = 1 (paper: 0.5)              */
@@ -73,7 +82,11 @@ typedef struct {
                             coarsest grid (Section 3.4; default 10, run to the full count)  */
   int sl_includes_gamma; /* 0: SL mass (1 - beta i); 1: (1 - (beta + gamma) i)               */
   int boundary_fix;      /* 1: coarse grids keep the low-side Dirichlet boundary at the
-                            fine position (ghost-point correction of the first row/col)     */
+                            fine position (ghost-point correction of the first row/col);
+                            Dirichlet problems only                                         */
+  int bc;                /* HELM_BC_*: the operator's boundary condition (default
+                            Dirichlet); every multigrid level is rediscretised with it,
+                            with kappa_l = sqrt(restricted kappa^2) and h_l = 2^l h       */
 } helm_mg_opts;
 
 /* Fill `o` with the defaults above (levels = 3). */

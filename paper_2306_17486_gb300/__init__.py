@@ -34,11 +34,16 @@ def _need(t, dtype, name):
         raise HelmError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
 
 
-def mg_opts(levels=3, beta=0.5, omega_jacobi=0.8, coarse_iters=10, sl_includes_gamma=False, boundary_fix=True):
+BOUNDARY_CONDITIONS = {"dirichlet": 0, "neumann": 1, "sommerfeld": 2}   # HELM_BC_*
+
+
+def mg_opts(levels=3, beta=0.5, omega_jacobi=0.8, coarse_iters=10, sl_includes_gamma=False, boundary_fix=True,
+            bc="dirichlet"):
     o = MgOpts()
     lib().helm_mg_opts_default(C.byref(o))
     o.levels, o.beta, o.omega_jacobi = levels, beta, omega_jacobi
     o.coarse_iters, o.sl_includes_gamma, o.boundary_fix = coarse_iters, int(sl_includes_gamma), int(boundary_fix)
+    o.bc = BOUNDARY_CONDITIONS[bc]
     return o
 
 
@@ -50,7 +55,9 @@ def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1, cnn
 
 
 class Problem:
-    """One slowness model kappa (CUDA float32 [ny, nx], absorbing layer included)."""
+    """One slowness model kappa (CUDA float32 [ny, nx], absorbing layer included).
+    Keyword options are those of `mg_opts`, among them bc = 'dirichlet' (the paper's
+    zero padding), 'neumann' or 'sommerfeld'."""
 
     def __init__(self, kappa: torch.Tensor, abl: int, omega_h: float, gamma0: float = 0.0, levels: int = 3,
                  **mg):

@@ -21,7 +21,7 @@ sz = C.c_size_t
 
 class MgOpts(C.Structure):
     _fields_ = [("levels", i32), ("beta", f64), ("omega_jacobi", f64), ("coarse_iters", i32),
-                ("sl_includes_gamma", i32), ("boundary_fix", i32)]
+                ("sl_includes_gamma", i32), ("boundary_fix", i32), ("bc", i32)]
 
 
 class FgmresOpts(C.Structure):

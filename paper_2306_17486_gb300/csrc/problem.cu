@@ -92,9 +92,14 @@ __device__ __forceinline__ double abl_profile(int i, int n, int abl) {
   return t * t;
 }
 
+// Boundary sides of node (y, x): 0 inside, 1 on an edge, 2 at a corner.
+__device__ __forceinline__ int boundary_sides(int y, int x, int ny, int nx) {
+  return (y == 0) + (y == ny - 1) + (x == 0) + (x == nx - 1);
+}
+
 __global__ void k_setup_fine(const float* __restrict__ kappa, int nx, int ny, int abl, double omega_h, double gamma0,
-                             float* __restrict__ gamma, float2* __restrict__ massA, double2* __restrict__ massA64, double* __restrict__ k2,
-                             double* __restrict__ g64) {
+                             int bc, float* __restrict__ gamma, float2* __restrict__ massA, double2* __restrict__ massA64,
+                             double* __restrict__ k2, double* __restrict__ g64) {
   long n = static_cast<long>(nx) * ny;
   for (long idx = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; idx < n;
        idx += static_cast<long>(gridDim.x) * blockDim.x) {
@@ -103,9 +108,16 @@ __global__ void k_setup_fine(const float* __restrict__ kappa, int nx, int ny, in
     double kk = static_cast<double>(kappa[idx]);
     kk = kk * kk;
     double m = omega_h * omega_h * kk;
+    double mr = m, mi = -m * g;
+    if (bc != HELM_BC_DIRICHLET) {
+      // ghost value c u_b per boundary side, folded into the mass term
+      const int nb = boundary_sides(y, x, ny, nx);
+      mr += nb;
+      if (bc == HELM_BC_SOMMERFELD) mi -= nb * omega_h * static_cast<double>(kappa[idx]);
+    }
     gamma[idx] = static_cast<float>(g);
-    massA[idx] = make_float2(static_cast<float>(m), static_cast<float>(-m * g));
-    massA64[idx] = make_double2(m, -m * g);
+    massA[idx] = make_float2(static_cast<float>(mr), static_cast<float>(mi));
+    massA64[idx] = make_double2(mr, mi);
     k2[idx] = kk;
     g64[idx] = g;
   }
@@ -131,19 +143,28 @@ __global__ void k_restrict_avg(const double* __restrict__ f, int nx, int ny, dou
   }
 }
 
-// SL mass (omega h_l)^2 k^2 (1 - (beta [+ gamma]) i), ghost-point boundary fix on the
-// first row/column of coarse levels, and the damped Jacobi inverse diagonal.
-__global__ void k_sl_mass(const double* __restrict__ k2, const double* __restrict__ g, int nx, int ny, double oh2,
-                          double beta, int use_gamma, double fix, double omega_j, float2* __restrict__ mass,
+// SL mass (omega h_l)^2 k^2 (1 - (beta [+ gamma]) i), then the boundary condition:
+// Dirichlet with the ghost-point boundary fix on the first row/column of coarse levels,
+// or the level's own Neumann / Sommerfeld ghost term (omega h_l, kappa_l = sqrt(k^2));
+// and the damped Jacobi inverse diagonal.
+__global__ void k_sl_mass(const double* __restrict__ k2, const double* __restrict__ g, int nx, int ny, double oh,
+                          double beta, int use_gamma, double fix, int bc, double omega_j, float2* __restrict__ mass,
                           float2* __restrict__ dinv) {
+  const double oh2 = oh * oh;
   long n = static_cast<long>(nx) * ny;
   for (long idx = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; idx < n;
        idx += static_cast<long>(gridDim.x) * blockDim.x) {
     int y = static_cast<int>(idx / nx), x = static_cast<int>(idx % nx);
     double sh = beta + (use_gamma ? g[idx] : 0.0);
     double mr = oh2 * k2[idx], mi = -oh2 * k2[idx] * sh;
-    if (y == 0) mr -= fix;
-    if (x == 0) mr -= fix;
+    if (bc == HELM_BC_DIRICHLET) {
+      if (y == 0) mr -= fix;
+      if (x == 0) mr -= fix;
+    } else {
+      const int nb = boundary_sides(y, x, ny, nx);
+      mr += nb;
+      if (bc == HELM_BC_SOMMERFELD) mi -= nb * oh * sqrt(k2[idx]);
+    }
     mass[idx] = make_float2(static_cast<float>(mr), static_cast<float>(mi));
     // omega_j / (4 - m)
     double dr = 4.0 - mr, di = -mi;
@@ -163,6 +184,7 @@ void helm_mg_opts_default(helm_mg_opts* o) {
   o->coarse_iters = 10;
   o->sl_includes_gamma = 0;
   o->boundary_fix = 1;
+  o->bc = HELM_BC_DIRICHLET;
 }
 
 const char* helm_last_error_string(void) { return helm::g_err; }
@@ -195,6 +217,10 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
   if (o.levels < 2 || o.levels > HELM_MAX_LEVELS || o.coarse_iters < 1 || o.coarse_iters > HELM_MAX_RESTART) {
     set_error("helm_problem_create: levels must be in [2,%d], coarse_iters in [1,%d]", HELM_MAX_LEVELS,
               HELM_MAX_RESTART);
+    return HELM_EINVAL;
+  }
+  if (o.bc != HELM_BC_DIRICHLET && o.bc != HELM_BC_NEUMANN && o.bc != HELM_BC_SOMMERFELD) {
+    set_error("helm_problem_create: bc must be HELM_BC_DIRICHLET, HELM_BC_NEUMANN or HELM_BC_SOMMERFELD");
     return HELM_EINVAL;
   }
   int div = 1 << o.levels;
@@ -248,14 +274,14 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
   if (cudaMemcpyAsync(p->kappa, kappa_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return fail(cuda_fail(cudaGetLastError(), "copy kappa"));
   int nb = static_cast<int>(std::min<long>(div_up(n0, 256), 4096));
-  HELM_LAUNCH("k_setup_fine", st, k_setup_fine<<<nb, 256, 0, st>>>(p->kappa, nx, ny, abl, omega_h, gamma0, p->gamma, p->massA, p->massA64, k2a, ga));
+  HELM_LAUNCH("k_setup_fine", st, k_setup_fine<<<nb, 256, 0, st>>>(p->kappa, nx, ny, abl, omega_h, gamma0, o.bc, p->gamma, p->massA, p->massA64, k2a, ga));
   for (int l = 0; l < o.levels; ++l) {
     double oh = omega_h * static_cast<double>(1 << l);
     double fix = (o.boundary_fix && l > 0) ? static_cast<double>((1 << l) - 1) : 0.0;
     long nl = p->npts(l);
     int nbl = static_cast<int>(std::min<long>(div_up(nl, 256), 4096));
-    HELM_LAUNCH("k_sl_mass", st, k_sl_mass<<<nbl, 256, 0, st>>>(k2a, ga, p->lnx[l], p->lny[l], oh * oh, o.beta, o.sl_includes_gamma, fix,
-                                   o.omega_jacobi, p->massSL[l], p->dinvSL[l]));
+    HELM_LAUNCH("k_sl_mass", st, k_sl_mass<<<nbl, 256, 0, st>>>(k2a, ga, p->lnx[l], p->lny[l], oh, o.beta, o.sl_includes_gamma, fix,
+                                   o.bc, o.omega_jacobi, p->massSL[l], p->dinvSL[l]));
     if (l + 1 < o.levels) {
       long nc = p->npts(l + 1);
       int nbc = static_cast<int>(std::min<long>(div_up(nc, 256), 4096));

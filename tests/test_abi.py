@@ -30,12 +30,18 @@ def test_host_side_validation_without_gpu(L):
     assert b"invalid" in L.helm_last_error_string()
     o = _lib.MgOpts()
     L.helm_mg_opts_default(ctypes.byref(o))
-    assert (o.levels, o.beta, o.omega_jacobi, o.coarse_iters, o.boundary_fix) == (3, 0.5, 0.8, 10, 1)
+    assert (o.levels, o.beta, o.omega_jacobi, o.coarse_iters, o.boundary_fix, o.bc) == (3, 0.5, 0.8, 10, 1, 0)
+    assert ctypes.sizeof(_lib.MgOpts) == 40
     o.levels = 4
     # 100 is not divisible by 2^4: shape error, before touching the device
     fake = ctypes.c_void_p(0x1000)
     assert L.helm_problem_create(fake, 100, 100, 8, 0.6, 0.0, ctypes.byref(o), None,
                                  ctypes.byref(ctypes.c_void_p())) == -2
+    o.bc = 3                                       # no such boundary condition
+    assert L.helm_problem_create(fake, 96, 96, 8, 0.6, 0.0, ctypes.byref(o), None,
+                                 ctypes.byref(ctypes.c_void_p())) == -1
+    assert b"bc must be" in L.helm_last_error_string()
+    o.bc = 0
     f = _lib.FgmresOpts()
     L.helm_fgmres_opts_default(ctypes.byref(f))
     assert (f.restart, f.rtol, f.maxit, f.warmup_iters, f.reorth, f.cnn_every) == (10, 1e-6, 2000, 3, 1, 1)
