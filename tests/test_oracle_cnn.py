@@ -111,6 +111,49 @@ def test_explicit_unet_is_the_implicit_one_with_an_identity_step():
     assert np.abs(net_r.forward(r, kf)[0] - net_e.forward(r, kf)[0]).max() > 1e-3 * np.abs(ei).max()
 
 
+def test_implicit_step_reaches_the_whole_map_and_the_explicit_network_does_not():
+    """Section 4.2: the implicit step widens the field of view.  A change of the solver
+    input at one corner of the I/2 map (I = 256) is followed to the opposite corner of
+    the output.
+    * The explicit U-Net's receptive field (3x3 convolutions at strides 1-8 and back,
+      about 105 pixels of the 128-pixel map) does not reach it: bitwise unchanged.
+    * Through the implicit layer the reach is set by the learned kernel.  With K = L +
+      1e-3 i delta (a weakly shifted Laplacian, Green's function decaying over about 30
+      coarse pixels) the change is orders of magnitude above that of the initial
+      L + iI (a kernel about a pixel wide, the change at rounding level).  Both go
+      through the same up path, whose random weights attenuate either equally."""
+    I, c0 = 256, 4
+    P = synth.random_params(cnn.param_spec(c0), seed=3, bn_jitter=0.2)
+    nk = P["s.imp.K"].shape[1]
+    lap = np.array([[0.0, -1.0, 0.0], [-1.0, 4.0, -1.0], [0.0, -1.0, 0.0]])
+    weak = np.zeros((3, 3))
+    weak[1, 1] = 1e-3
+    P_long = dict(P)
+    P_long["s.imp.K"] = np.stack([np.broadcast_to(lap, (nk, 3, 3)), np.broadcast_to(weak, (nk, 3, 3))]).copy()
+    Pe = {k: v for k, v in P.items() if k != "s.imp.K"}
+    rng = np.random.default_rng(4)
+    kf = rng.uniform(0.0625, 1.0, size=(1, 2, I, I))
+    x0 = rng.standard_normal((1, 2, I // 2, I // 2))
+    x1 = x0.copy()
+    x1[0, :, 0, 0] += 1.0
+
+    def far_change(params, implicit):
+        net = cnn.Network(params, c0=c0, implicit=implicit)
+        outs = []
+        for x in (x0, x1):
+            tp = cnn.Tape(params, record=False)
+            encs = cnn.encoder(tp, cnn.Var(kf), False, net.running)
+            ghat = net.ghat(cnn.coarsest_size(I, True)) if implicit else None
+            outs.append(cnn.solver(tp, cnn.Var(x), encs, ghat, False, net.running, True).a)
+        return np.abs(outs[1] - outs[0])[0, :, -8:, -8:].max(), np.abs(outs[0]).max()
+
+    d_expl, _ = far_change(Pe, False)
+    d_init, _ = far_change(P, True)
+    d_long, scale = far_change(P_long, True)
+    assert d_expl == 0.0
+    assert d_long > 100 * d_init and d_long > 1e3 * np.finfo(float).eps * scale, (d_long, d_init)
+
+
 def test_bn_eval_folding_equivalence():
     """Eval-mode BN equals the folded affine a*x + c."""
     rng = np.random.default_rng(3)
