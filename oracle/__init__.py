@@ -21,6 +21,7 @@ Pins: every function above is checked against something other than itself (assem
 matrices, dense LU, closed forms, LFA, finite differences, the paper's printed
 constants) by the `-m "not gpu"` tests.  Parity unpinned: the results of training and
 the iteration counts of a trained network, implicit or explicit (the paper's datasets
-and weights are not available); `training.composed_preconditioner` is pinned only as a
-composition of pinned parts.
+and weights are not available).  `training.composed_preconditioner` is pinned by the
+special cases its algebra fixes: a zero network output gives the plain V-cycle, the
+exact error is returned unchanged, and z - e is the V-cycle of the remaining residual.
 """

@@ -154,6 +154,39 @@ def test_implicit_step_reaches_the_whole_map_and_the_explicit_network_does_not()
     assert d_long > 100 * d_init and d_long > 1e3 * np.finfo(float).eps * scale, (d_long, d_init)
 
 
+def test_composed_preconditioner_reduces_to_its_parts():
+    """z = e + V(r - A e) (Section 4.1, multiplicative composition).  A network whose
+    output is zero gives exactly the plain V-cycle.  One whose output is the exact error
+    A^-1 r leaves nothing for the V-cycle to correct (V(0) = 0), so z = A^-1 r.  For any
+    output e, z - e is the V-cycle of the remaining residual."""
+    N, abl = 32, 4
+    p = hz.Problem(synth.grf_kappa(N - 2 * abl, abl, 4.0, 3), abl)
+    V = mg.SLMultigrid(p, 3)
+    r = synth.random_complex((N, N), 1)
+
+    class FixedOutput:
+        def __init__(self, f):
+            self.f = f
+
+        def forward(self, rb, kfeat, train=False):
+            return self.f(rb), None
+
+    zero = tr.composed_preconditioner(p, FixedOutput(np.zeros_like), None, V)
+    assert np.array_equal(zero(r), V(r))
+    assert not np.any(V(np.zeros_like(r)))
+    Ad = mg.dense_matrix(p.mass_A)
+
+    def exact(rb):
+        return np.stack([np.linalg.solve(Ad, v.ravel()).reshape(N, N) for v in rb])
+
+    e = exact(r[None])[0]
+    z = tr.composed_preconditioner(p, FixedOutput(exact), None, V)(r)
+    assert np.linalg.norm(z - e) <= 1e-10 * np.linalg.norm(e)
+    other = 0.3 * synth.random_complex((1, N, N), 2)
+    z = tr.composed_preconditioner(p, FixedOutput(lambda rb: other), None, V)(r)
+    assert np.allclose(z - other[0], V(r - p.A(other[0])), rtol=0, atol=1e-13 * np.abs(z).max())
+
+
 def test_bn_eval_folding_equivalence():
     """Eval-mode BN equals the folded affine a*x + c."""
     rng = np.random.default_rng(3)
