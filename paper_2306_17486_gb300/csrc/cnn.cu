@@ -287,6 +287,14 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
       meta.push_back(static_cast<int>(c->params[b.pg].offset));
       meta.push_back(static_cast<int>(c->params[b.pb].offset));
     }
+    if (!c->gscratch) {   // freed by a failed enlargement: the small table needs its head
+      if (cudaMalloc(&c->gscratch, 4096 * sizeof(float2)) != cudaSuccess) {
+        c->gscratch = nullptr;
+        set_error("cnn: out of device memory");
+        return HELM_ENOMEM;
+      }
+      c->gscratch_elems = 4096;
+    }
     int* dmeta = reinterpret_cast<int*>(c->gscratch);  // reuse scratch head for the small table
     HELM_CUDA(cudaMemcpyAsync(dmeta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     HELM_LAUNCH("k_fold_bn", st,
@@ -305,7 +313,10 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
     const size_t need = greens_scratch_elems(m, nk);
     if (need > c->gscratch_elems) {
       cudaFree(c->gscratch);
+      c->gscratch = nullptr;
+      c->gscratch_elems = 0;
       if (cudaMalloc(&c->gscratch, need * sizeof(float2)) != cudaSuccess) {
+        c->gscratch = nullptr;
         set_error("cnn: out of memory for the Green's function scratch");
         return HELM_ENOMEM;
       }
@@ -317,7 +328,10 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
       return HELM_ENOMEM;
     }
     int rc = launch_greens(c->params_dev + K.offset, nk, m, 1e-5f, c->desc.literal_green, c->gscratch, g, st);
-    if (rc) return rc;
+    if (rc) {
+      cudaFree(g);
+      return rc;
+    }
     c->ghat[m] = g;
   }
   return HELM_OK;
@@ -439,6 +453,8 @@ int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
     cudaFree(c->enc_arena);
     c->enc_arena = nullptr;
     if (cudaMalloc(&c->enc_arena, c->enc_plan.arena) != cudaSuccess) {
+      c->enc_arena = nullptr;
+      c->enc_I = 0;
       set_error("cnn: out of memory for the encodings");
       return HELM_ENOMEM;
     }
