@@ -262,17 +262,18 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
       return fail(HELM_ENOMEM);
     }
   }
-  double *k2a, *k2b, *ga, *gb;
-  if (cudaMalloc(&k2a, n0 * 8) != cudaSuccess) return fail(HELM_ENOMEM);
-  tmp.push_back(k2a);
-  if (cudaMalloc(&k2b, n0 * 8) != cudaSuccess) return fail(HELM_ENOMEM);
-  tmp.push_back(k2b);
-  if (cudaMalloc(&ga, n0 * 8) != cudaSuccess) return fail(HELM_ENOMEM);
-  tmp.push_back(ga);
-  if (cudaMalloc(&gb, n0 * 8) != cudaSuccess) return fail(HELM_ENOMEM);
-  tmp.push_back(gb);
-  if (cudaMemcpyAsync(p->kappa, kappa_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return fail(cuda_fail(cudaGetLastError(), "copy kappa"));
+  // FP64 kappa^2 and gamma pyramids (two levels at a time), freed at the end
+  double* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (double*& b : buf) {
+    if (cudaMalloc(&b, n0 * 8) != cudaSuccess) {
+      set_error("helm_problem_create: out of device memory for the setup pyramids");
+      return fail(HELM_ENOMEM);
+    }
+    tmp.push_back(b);
+  }
+  double *k2a = buf[0], *k2b = buf[1], *ga = buf[2], *gb = buf[3];
+  cudaError_t ce = cudaMemcpyAsync(p->kappa, kappa_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "copy kappa"));
   int nb = static_cast<int>(std::min<long>(div_up(n0, 256), 4096));
   HELM_LAUNCH("k_setup_fine", st, k_setup_fine<<<nb, 256, 0, st>>>(p->kappa, nx, ny, abl, omega_h, gamma0, o.bc, p->gamma, p->massA, p->massA64, k2a, ga));
   for (int l = 0; l < o.levels; ++l) {
