@@ -4,7 +4,8 @@ runs `--warmup` untimed repetitions and `--reps` repetitions of one hot-path cal
 prints the library's per-kernel CUDA-event times for the repetitions.
 
     python -m paper_2306_17486_gb300.profile_case apply|vcycle|cnn|precond|solve [--batch B]
-        [--reps R] [--warmup W] [--weights npz] [--maxit K]
+        [--reps R] [--warmup W] [--weights npz] [--maxit K] [--bc dirichlet|neumann|sommerfeld]
+        [--explicit]
 
   apply    Helmholtz matvec y = h^2 A x on B random vectors
   vcycle   one SL V(1,1) cycle on B random residuals
@@ -12,6 +13,9 @@ prints the library's per-kernel CUDA-event times for the repetitions.
   precond  the composed preconditioner z = e + V(r - A e)
   solve    FGMRES(10) with the composed preconditioner (--mg-only: V-cycle alone) on B
            point sources, at most --maxit iterations
+--bc selects the boundary condition of the problem; --explicit times the explicit U-Net
+(the network without the implicit step, randomly initialised: its timing does not depend
+on the weights).
 """
 from __future__ import annotations
 
@@ -36,6 +40,8 @@ def main():
                                                       "cnn_grf_multiscale.npz"))
     ap.add_argument("--maxit", type=int, default=50)
     ap.add_argument("--mg-only", action="store_true")
+    ap.add_argument("--bc", default="dirichlet", choices=["dirichlet", "neumann", "sommerfeld"])
+    ap.add_argument("--explicit", action="store_true")
     a = ap.parse_args()
     sys.path.insert(0, ROOT)
     import synth
@@ -44,15 +50,19 @@ def main():
     from ._lib import lib
     dev = "cuda"
     kap = synth.grf_kappa(512, 32, 8.0, seed=10)
-    p = Problem(torch.tensor(kap, dtype=torch.float32, device=dev), 32, 2 * np.pi / 10 / float(kap.max()), levels=4)
+    p = Problem(torch.tensor(kap, dtype=torch.float32, device=dev), 32, 2 * np.pi / 10 / float(kap.max()), levels=4,
+                bc=a.bc)
     B = a.batch
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     r = torch.randn((B, 576, 576), dtype=torch.complex64, device=dev, generator=g)
     net = None
     if a.case in ("cnn", "precond") or (a.case == "solve" and not a.mg_only):
-        net = Cnn(skip_threshold=256)
-        T.load_weights(net, a.weights)
+        net = Cnn(skip_threshold=256, explicit_unet=a.explicit)
+        if a.explicit:
+            net.load_dict(synth.random_params(T.init_spec(net), seed=0))
+        else:
+            T.load_weights(net, a.weights)
         net.set_problem(p)
     if a.case == "solve":
         b = torch.tensor(synth.random_point_sources(576, 32, B, seed=1000), dtype=torch.complex64, device=dev)
