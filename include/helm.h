@@ -158,8 +158,9 @@ int helm_slmg_vcycle(const helm_problem* p, const void* r, void* z, int batch, v
  *     returns HELM_EWORKSPACE before launching anything.
  *   - Nothing in the scratch has to start at zero: every element is written before it
  *     is read within one call.
- *   - The first call on a device looks up the array's address (cudaGetSymbolAddress);
- *     make that first call before any stream capture.
+ *   - The first call on a device looks up the array's address (cudaGetSymbolAddress)
+ *     and keeps it for the life of the process; make that first call before any stream
+ *     capture, and do not use this entry point on a device after cudaDeviceReset.
  *   - All calls on one device share the one array: calls that may overlap in time
  *     (different streams, or threads without ordering) race on it.  Order them on one
  *     stream.

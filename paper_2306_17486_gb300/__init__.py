@@ -34,6 +34,38 @@ def _need(t, dtype, name):
         raise HelmError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
 
 
+def _grid(p, t, dtype, name) -> int:
+    """Check that t is a contiguous CUDA tensor of `dtype` on the problem's device with
+    shape [ny, nx] or [B, ny, nx] of problem p; returns the batch B.  The library
+    builds its tensor maps and writes its outputs from p's grid and B, so a tensor of
+    any other shape would be read or written out of bounds."""
+    _need(t, dtype, name)
+    if t.device != p.device:
+        raise HelmError(f"{name} is on {t.device}, the problem on {p.device}")
+    if t.dim() not in (2, 3) or tuple(t.shape[-2:]) != (p.ny, p.nx) or (t.dim() == 3 and t.shape[0] < 1):
+        raise HelmError(f"{name} has shape {tuple(t.shape)}; expected [B, {p.ny}, {p.nx}] or [{p.ny}, {p.nx}]")
+    return t.shape[0] if t.dim() == 3 else 1
+
+
+def _out(p, ref, out, dtype, name):
+    """The output buffer: a new tensor shaped like `ref`, or the caller's `out`, which must
+    have ref's shape, `dtype` and device and must not alias ref."""
+    if out is None:
+        return torch.empty(ref.shape, dtype=dtype, device=ref.device)
+    _grid(p, out, dtype, name)
+    if tuple(out.shape) != tuple(ref.shape):
+        raise HelmError(f"{name} has shape {tuple(out.shape)}, expected {tuple(ref.shape)}")
+    if out.data_ptr() == ref.data_ptr():
+        raise HelmError(f"{name} must not alias the input")
+    return out
+
+
+def _batch_vec(t, B, dtype, name, device):
+    _need(t, dtype, name)
+    if t.device != device or t.numel() != B:
+        raise HelmError(f"{name} must hold {B} entries on {device}")
+
+
 BOUNDARY_CONDITIONS = {"dirichlet": 0, "neumann": 1, "sommerfeld": 2}   # HELM_BC_*
 
 
@@ -107,18 +139,18 @@ class Problem:
 
 def helmholtz_apply(p: Problem, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
     """y = h^2 A x for complex64 x [B, ny, nx]."""
-    _need(x, torch.complex64, "x")
-    y = torch.empty_like(x) if y is None else y
-    B = x.shape[0] if x.dim() == 3 else 1
+    B = _grid(p, x, torch.complex64, "x")
+    y = _out(p, x, y, torch.complex64, "y")
     check(lib().helm_helmholtz_apply(p.handle, _ptr(x), _ptr(y), B, _stream()), "helm_helmholtz_apply")
     return y
 
 
 def helmholtz_residual_fp64(p: Problem, b: torch.Tensor, x: torch.Tensor):
     """(r, ||r||^2) with r = b - h^2 A x evaluated in FP64 (x complex128)."""
-    _need(b, torch.complex64, "b")
-    _need(x, torch.complex128, "x")
-    B = b.shape[0] if b.dim() == 3 else 1
+    B = _grid(p, b, torch.complex64, "b")
+    _grid(p, x, torch.complex128, "x")
+    if tuple(x.shape) != tuple(b.shape):
+        raise HelmError(f"x has shape {tuple(x.shape)}, b {tuple(b.shape)}")
     r = torch.empty_like(b)
     nr = torch.empty(B, dtype=torch.float64, device=b.device)
     ws = p.workspace(B)
@@ -129,9 +161,8 @@ def helmholtz_residual_fp64(p: Problem, b: torch.Tensor, x: torch.Tensor):
 
 def slmg_vcycle(p: Problem, r: torch.Tensor, z: torch.Tensor | None = None) -> torch.Tensor:
     """z = V(r), one shifted-Laplacian V(1,1) cycle."""
-    _need(r, torch.complex64, "r")
-    z = torch.empty_like(r) if z is None else z
-    B = r.shape[0] if r.dim() == 3 else 1
+    B = _grid(p, r, torch.complex64, "r")
+    z = _out(p, r, z, torch.complex64, "z")
     ws = p.workspace(B)
     check(lib().helm_slmg_vcycle(p.handle, _ptr(r), _ptr(z), B, _ptr(ws), ws.numel(), _stream()),
           "helm_slmg_vcycle")
@@ -142,9 +173,8 @@ def slmg_vcycle_static(p: Problem, r: torch.Tensor, z: torch.Tensor | None = Non
     """z = V(r) like slmg_vcycle, using the library's fixed device scratch instead of a
     workspace (for callers that cannot allocate); raises if the batch needs more scratch
     than the library holds."""
-    _need(r, torch.complex64, "r")
-    z = torch.empty_like(r) if z is None else z
-    B = r.shape[0] if r.dim() == 3 else 1
+    B = _grid(p, r, torch.complex64, "r")
+    z = _out(p, r, z, torch.complex64, "z")
     check(lib().helm_slmg_vcycle_static(p.handle, _ptr(r), _ptr(z), B, _stream()), "helm_slmg_vcycle_static")
     return z
 
@@ -154,17 +184,18 @@ def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn
     """Solve h^2 A x = b (b complex64 [B, ny, nx]); x complex128 (in: x0, out: solution).
     Returns (x, stats) with stats a numpy structured array (iters, status, rel_res_est,
     rel_res_true) per right-hand side."""
-    _need(b, torch.complex64, "b")
-    B = b.shape[0]
+    B = _grid(p, b, torch.complex64, "b")
     if x is None:
         x = torch.zeros(b.shape, dtype=torch.complex128, device=b.device)
-    _need(x, torch.complex128, "x")
+    _grid(p, x, torch.complex128, "x")
+    if tuple(x.shape) != tuple(b.shape):
+        raise HelmError(f"x has shape {tuple(x.shape)}, b {tuple(b.shape)}")
     stats = torch.zeros(B * STATS_DTYPE.itemsize, dtype=torch.uint8, device=b.device)
     ws = p.workspace(B, restart, cnn)
     o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth, cnn_every)
     caps = None
     if maxit_per_rhs is not None:
-        _need(maxit_per_rhs, torch.int32, "maxit_per_rhs")
+        _batch_vec(maxit_per_rhs, B, torch.int32, "maxit_per_rhs", b.device)
         caps = maxit_per_rhs
     check(lib().helm_fgmres_solve(p.handle, cnn.handle if cnn is not None else None, _ptr(b), _ptr(x), B,
                                   C.byref(o), _ptr(caps), _ptr(stats), _ptr(ws), ws.numel(), _stream()),
@@ -192,10 +223,20 @@ def conv_bf16(x: torch.Tensor, w: torch.Tensor, mode: str = "s1", scale=None, sh
     w FP32 in PyTorch module layout.  Returns (y BF16 NHWC, yraw FP32 NHWC or None)."""
     _need(x, torch.bfloat16, "x")
     _need(w, torch.float32, "w")
+    if x.dim() != 4 or w.device != x.device:
+        raise HelmError("x must be BF16 NHWC [B, H, W, Cin]; w on the same device")
     B, H, W, Ci = x.shape
-    taps = 1 if w.dim() == 2 else 9
+    if w.dim() == 2:
+        taps = 1
+    elif w.dim() == 4 and tuple(w.shape[2:]) == (3, 3):
+        taps = 9
+    else:
+        raise HelmError(f"w has shape {tuple(w.shape)}; expected [Co, Ci] or a 3x3 kernel")
     m = CONV_MODES[mode]
-    Co = w.shape[0] if (taps == 1 or m in (0, 1)) else w.shape[1]
+    transposed = taps == 9 and m in (2, 3)
+    Co = w.shape[1] if transposed else w.shape[0]
+    if (w.shape[0] if transposed else w.shape[1]) != Ci:
+        raise HelmError(f"w has shape {tuple(w.shape)} for {Ci} input channels")
     if taps == 1:
         Ho, Wo = H, W
     elif m == 1:
@@ -204,6 +245,18 @@ def conv_bf16(x: torch.Tensor, w: torch.Tensor, mode: str = "s1", scale=None, sh
         Ho, Wo = 2 * H, 2 * W
     else:
         Ho, Wo = H, W
+    for v, nm in ((scale, "scale"), (shift, "shift")):
+        if v is not None:
+            _batch_vec(v, Co, torch.float32, nm, x.device)
+    if add1 is not None:
+        _need(add1, torch.bfloat16, "add1")
+        if tuple(add1.shape) != (B, Ho, Wo, Co) or add1.device != x.device:
+            raise HelmError(f"add1 must be [{B}, {Ho}, {Wo}, {Co}] on {x.device}")
+    if add2 is not None:
+        _need(add2, torch.bfloat16, "add2")
+        if add2.dim() != 4 or add2.shape[0] not in (1, B) or tuple(add2.shape[1:]) != (Ho, Wo, Co) \
+                or add2.device != x.device:
+            raise HelmError(f"add2 must be [{B} or 1, {Ho}, {Wo}, {Co}] on {x.device}")
     y = torch.empty((B, Ho, Wo, Co), dtype=torch.bfloat16, device=x.device)
     yr = torch.empty((B, Ho, Wo, Co), dtype=torch.float32, device=x.device) if raw else None
     ws = torch.empty(taps * max(16, (Ci + 15) // 16 * 16) * Co * 2 + 4096, dtype=torch.uint8, device=x.device)
@@ -322,8 +375,7 @@ class Cnn:
 
     def apply(self, p: Problem, r: torch.Tensor, train: bool = False, ws: torch.Tensor | None = None):
         """e = s Net(r / s), s = RMS of r over the grid."""
-        _need(r, torch.complex64, "r")
-        B = r.shape[0]
+        B = _grid(p, r, torch.complex64, "r")
         e = torch.empty_like(r)
         ws = p.workspace(B, 10, self) if ws is None else ws
         check(lib().helm_cnn_apply(p.handle, self.handle, _ptr(r), _ptr(e), B, int(train), _ptr(ws), ws.numel(),
@@ -332,8 +384,7 @@ class Cnn:
 
     def precond(self, p: Problem, r: torch.Tensor):
         """z = e + V(r - A e)."""
-        _need(r, torch.complex64, "r")
-        B = r.shape[0]
+        B = _grid(p, r, torch.complex64, "r")
         z = torch.empty_like(r)
         ws = p.workspace(B, 10, self)
         check(lib().helm_cnn_precond_apply(p.handle, self.handle, _ptr(r), _ptr(z), B, _ptr(ws), ws.numel(),
@@ -354,9 +405,10 @@ class Cnn:
         """Training-mode forward (batch-statistics BN; saves activations for backward).
         `p` is one Problem or a list of Problems: sample b then belongs to
         p[b // (B // len(p))]."""
-        _need(r, torch.complex64, "r")
-        B = r.shape[0]
         probs = list(p) if isinstance(p, (list, tuple)) else [p]
+        B = _grid(probs[0], r, torch.complex64, "r")
+        if B % len(probs):
+            raise HelmError(f"batch {B} is not divisible by the {len(probs)} slowness models")
         ws = self.train_workspace(probs[0], B, len(probs))
         e = torch.empty_like(r)
         arr = (C.c_void_p * len(probs))(*[q.handle.value for q in probs])
@@ -367,10 +419,10 @@ class Cnn:
         return e
 
     def backward(self, p, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None) -> torch.Tensor:
-        _need(grad_e, torch.complex64, "grad_e")
-        B = grad_e.shape[0]
-        g = torch.empty_like(self.params) if grad_params is None else grad_params
         p = p[0] if isinstance(p, (list, tuple)) else p
+        B = _grid(p, grad_e, torch.complex64, "grad_e")
+        g = torch.empty_like(self.params) if grad_params is None else grad_params
+        _batch_vec(g, self.nparams, torch.float32, "grad_params", self.params.device)
         ws = self.train_workspace(p, B, getattr(self, "_train_nprob", 1))
         check(lib().helm_cnn_precond_backward(p.handle, self.handle, _ptr(grad_e), _ptr(g), B, _ptr(ws), ws.numel(),
                                               _stream()), "helm_cnn_precond_backward")
@@ -381,6 +433,8 @@ def mse_loss(e_pred: torch.Tensor, e_true: torch.Tensor, grad: bool = True):
     """Eq. (16) on the device: (loss tensor (float64, shape [1]), gradient or None)."""
     _need(e_pred, torch.complex64, "e_pred")
     _need(e_true, torch.complex64, "e_true")
+    if e_true.shape != e_pred.shape or e_true.device != e_pred.device or e_pred.dim() < 2:
+        raise HelmError(f"e_pred {tuple(e_pred.shape)} and e_true {tuple(e_true.shape)} must match, batch first")
     B = e_pred.shape[0]
     loss = torch.empty(1, dtype=torch.float64, device=e_pred.device)
     g = torch.empty_like(e_pred) if grad else None
@@ -424,9 +478,8 @@ class CnnFunction(torch.autograd.Function):
 def datagen_pairs(p: Problem, x: torch.Tensor, iters: torch.Tensor, max_iters: int = 20, normalise: bool = True):
     """Eq. (17) on the device: (e, r) complex64 for random x [B, N, N] (complex64) and
     per-sample FGMRES iteration counts `iters` (int32 CUDA tensor)."""
-    _need(x, torch.complex64, "x")
-    _need(iters, torch.int32, "iters")
-    B = x.shape[0]
+    B = _grid(p, x, torch.complex64, "x")
+    _batch_vec(iters, B, torch.int32, "iters", x.device)
     n = C.c_size_t()
     check(lib().helm_datagen_workspace_size(p.handle, B, max_iters, C.byref(n)), "datagen_workspace_size")
     ws = getattr(p, "_dws", None)

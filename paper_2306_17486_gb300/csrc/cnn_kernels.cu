@@ -582,7 +582,7 @@ int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat,
     set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
     return HELM_ESHAPE;
   }
-  static unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<bf16, bf16>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit", st,
               k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(x, m, C, ghat, 0, y, 0,
@@ -597,7 +597,7 @@ int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* 
     set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
     return HELM_ESHAPE;
   }
-  static unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<float, float>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit_adj", st,
               k_implicit<float, float><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(gy, m, C, ghat, 1, gx, 1,

@@ -965,7 +965,7 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
       if (rc) return rc;
       const int m = pl.m, n = 2 * m, nk = in.C / 2;
       const size_t sm = implicit_smem(m) + static_cast<size_t>(n) * n * sizeof(float2);
-      static unsigned long long attr_done = 0;
+      static std::atomic<unsigned long long> attr_done{0};
       if ((rc = smem_attr_once(k_implicit_kgrad, 200 * 1024, &attr_done))) return rc;
       HELM_LAUNCH("k_implicit_kgrad", st,
                   k_implicit_kgrad<<<dim3(nk, in.B), 256, sm, st>>>(static_cast<const bf16*>(ptr[L.in]), dY, m, in.C,

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -159,14 +160,16 @@ int sm_count(int* out);
 // Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device, once
 // per device: `done` is the caller's bitmask of devices already configured (the
 // attribute belongs to a device, so a process using several GPUs sets it on each).
+// The mask is atomic: host threads calling into the library concurrently at most
+// repeat the (idempotent) attribute call.
 template <class K>
-inline int smem_attr_once(K* kernel, int bytes, unsigned long long* done) {
+inline int smem_attr_once(K* kernel, int bytes, std::atomic<unsigned long long>* done) {
   int dev = 0;
   HELM_CUDA(cudaGetDevice(&dev));
   const unsigned long long bit = 1ull << (dev & 63);
-  if (!(*done & bit)) {
+  if (!(done->load(std::memory_order_acquire) & bit)) {
     HELM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    *done |= bit;
+    done->fetch_or(bit, std::memory_order_acq_rel);
   }
   return HELM_OK;
 }

@@ -410,7 +410,7 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     helm::set_error("conv: shared memory %zu bytes exceeds the per-CTA limit (grid row too wide)", smem);
     return HELM_ESHAPE;
   }
-  static unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   int rc = helm::smem_attr_once(k_conv_tc<CS, COUT, TAPS, PH, MTR>, 227 * 1024, &attr_done);
   int nsm = 0;
   if (!rc) rc = helm::sm_count(&nsm);

@@ -309,7 +309,7 @@ int launch_ib_t(const IbArgs& a0, cudaStream_t st) {
   a.tiles_x = helm::div_up(a.W, IB_TW);
   a.tiles_y = helm::div_up(a.H, IB_TH);
   a.ntiles = a.tiles_x * a.tiles_y * a.B;
-  static unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   int rc = helm::smem_attr_once(k_ib_fused<C>, static_cast<int>(Cfg::SMEM), &attr_done);
   int nsm = 0;
   if (!rc) rc = helm::sm_count(&nsm);

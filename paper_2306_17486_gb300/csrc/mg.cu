@@ -652,7 +652,7 @@ int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, 
     const int cnx = p->lnx[L - 1], cny = p->lny[L - 1];
     const size_t smem = cluster_smem_bytes(cnx, cny);
     if (p->mg.coarse_iters == CL_K && smem <= 200 * 1024) {
-      static unsigned long long attr_done = 0;
+      static std::atomic<unsigned long long> attr_done{0};
       if ((rc = smem_attr_once(k_coarse_gmres_cluster<CL_K>, 200 * 1024, &attr_done))) return rc;
       const int rows_per = (cny + CL_SIZE - 1) / CL_SIZE;
       HELM_LAUNCH("k_coarse_gmres_cluster", st,

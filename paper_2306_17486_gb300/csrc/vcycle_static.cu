@@ -8,7 +8,9 @@
 // allocates nothing and calls no allocating CUDA or library routine.  Its scratch is a
 // file-scope __device__ array of HELM_VCYCLE_STATIC_BYTES, present on every device the
 // library's module is loaded on; its address is taken once per device, on the first
-// call, with cudaGetSymbolAddress.
+// call, with cudaGetSymbolAddress, and kept for the life of the process.  After a
+// cudaDeviceReset (which unloads the module and its array) that kept address is stale,
+// so this entry point must not be used on a device that has been reset.
 #include <mutex>
 
 #include "problem.h"
