@@ -182,6 +182,13 @@ typedef struct {
                        j mod cnn_every == 0, the V-cycle alone on the others (FGMRES admits
                        a different preconditioner per step); 1 = every step, the paper's
                        method (default); must be >= 1                                      */
+  int fallback;     /* with a CNN, 1 (default): a right-hand side falls back to the plain
+                       V-cycle for the rest of its solve when a restart cycle with the
+                       network reduces its true residual by less than 5 %, or when a step
+                       with the network gives a non-finite Arnoldi column (that step is
+                       discarded, the cycle ends with the steps before it); 0: the network
+                       stays in use (a stalled RHS runs on to maxit, a non-finite column
+                       ends the RHS with HELM_STATUS_NONFINITE)                           */
 } helm_fgmres_opts;
 
 /* Per-RHS result. */
@@ -223,6 +230,31 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b,
 int helm_conv_bf16(const void* x, int batch, int hi, int wi, int cin, const float* w, int cout, int taps, int mode,
                    const float* scale, const float* shift, int act, const void* add1, const void* add2,
                    int add2_bcast, void* y, float* yraw, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * One evaluation-mode inverted bottleneck of the solver network (Section 4.4: the
+ * MobileNetV2 block, expansion 6) in one fused kernel, the layer the network executes:
+ *   y = x + BN2(P softplus(BN1(dw3x3(softplus(BN0(E x))))))
+ * x, y: BF16 NHWC [batch][h][w][c], distinct; c = 16, 32 or 64.  Weights FP32 in the
+ * PyTorch module layouts: w_exp [6c][c] (1x1), w_dw [6c][3][3] (depthwise, zero
+ * padding), w_proj [c][6c] (1x1); the 1x1 weights are rounded to BF16 and the depthwise
+ * weights to FP16 inside.  bn0, bn1 (FP32 [2][6c]) and bn2 (FP32 [2][c]) are folded
+ * evaluation-mode BatchNorms, scale then shift.  ws: device scratch for the packed
+ * weights (>= 4 c 6c + 512 bytes; HELM_EWORKSPACE otherwise).
+ */
+int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const float* w_exp, const float* bn0,
+                 const float* w_dw, const float* bn1, const float* w_proj, const float* bn2, void* y, void* ws,
+                 size_t ws_bytes, void* stream);
+
+/*
+ * The implicit layer (Section 4.2, Eq. 14) as the network executes it: channel k and
+ * k + c/2 of x (BF16 NHWC [batch][m][m][c], c a multiple of 8) form complex channel k,
+ * which is zero-padded to 2m x 2m, transformed, multiplied by ghat[k] (complex64
+ * [c/2][2m][2m], the Green's function of Eq. 15 after crop and DFT, as returned by
+ * helm_cnn_get_ghat), transformed back and cropped to the top-left m x m block; y has
+ * x's layout, distinct from x.  HELM_ESHAPE for m beyond the shared-memory limit.
+ */
+int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat, void* y, void* stream);
 
 /* Number of kernels the library has launched in this process (all devices). */
 unsigned long long helm_launch_count(void);
@@ -297,12 +329,20 @@ int helm_cnn_train_workspace_size(const helm_problem* p, const helm_cnn* c, int 
 int helm_cnn_train_forward(const helm_problem* const* probs, int nprob, helm_cnn* c, const void* r, void* e,
                            int batch, void* ws, size_t ws_bytes, void* stream);
 
-/* Backward of the last training-mode helm_cnn_apply that used the same workspace:
- * grad_e (complex64 [batch][N][N], dLoss/dRe e + i dLoss/dIm e) -> grad_params (FP32,
- * parameter layout, overwritten).  Covers the solver and the encoder (the encodings
- * receive the batch sum of their gradients); the V-cycle is not differentiated. */
-int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* grad_e, float* grad_params, int batch,
-                              void* ws, size_t ws_bytes, void* stream);
+/* Backward of the last training-mode forward (helm_cnn_train_forward or
+ * helm_cnn_apply(train = 1)) that used the same workspace, for the network part
+ * e = s Net(r / s), s = RMS(r) of Section 4.1 (Eq. 16's SolverNet; the V-cycle is not
+ * differentiated):
+ *   grad_e      complex64 [batch][N][N], dLoss/dRe e + i dLoss/dIm e
+ *   grad_params FP32 in the parameter layout, overwritten; covers the solver and the
+ *               encoder (the encodings receive the batch sum of their gradients)
+ *   grad_r      nullable; complex64 [batch][N][N] receives dLoss/dRe r + i dLoss/dIm r,
+ *               the scale s's own dependence on r included (a zero sample gets zero)
+ *   r           the forward's input (complex64, caller-owned); needed only with grad_r
+ * HELM_EINVAL if grad_r is given without r or aliases it; HELM_ESTATE without a
+ * preceding training forward. */
+int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* r, const void* grad_e, void* grad_r,
+                              float* grad_params, int batch, void* ws, size_t ws_bytes, void* stream);
 
 /* Eq. (16): loss = (1/batch) sum |e_pred - e_true|^2 over n complex entries (all
  * batch items), written as float64 to loss_dev; grad (nullable, complex64 like e_pred)
@@ -313,6 +353,23 @@ int helm_mse_loss(const void* e_pred, const void* e_true, long n, int batch, dou
 /* One Adam step (bias-corrected, step >= 1) on n FP32 parameters, moments m, v. */
 int helm_adam_step(float* params, const float* grads, float* m, float* v, long n, double lr, double beta1,
                    double beta2, double eps, int step, void* stream);
+
+/* Save the network to the file `path`: its descriptor, the FP32 parameters (the vector
+ * set by helm_cnn_set_params), the BN running statistics and the Green's function G_hat
+ * of every coarsest size m the handle holds for these parameters (Section 4.2: G_hat is
+ * computed from the learned kernel once and stored as part of the network), followed by
+ * a hash of the contents.  Host I/O; synchronises `stream`.  HELM_ESTATE without
+ * parameters, HELM_EINVAL if the file cannot be written. */
+int helm_cnn_save(helm_cnn* c, const char* path, void* stream);
+
+/* Load a file written by helm_cnn_save into a handle created with the same descriptor:
+ * the parameters are copied to params_dev (caller-owned device FP32 [num_params], which
+ * becomes the handle's parameter vector as if passed to helm_cnn_set_params), the
+ * running statistics into the handle, and the stored G_hat become the handle's Green's
+ * functions without an Eq. 15 rebuild.  HELM_EINVAL if the file is missing, truncated,
+ * fails its hash, or was saved from another descriptor or parameter table (then
+ * nothing is changed); synchronises `stream`.  Needs helm_cnn_set_problem afterwards. */
+int helm_cnn_load(helm_cnn* c, const char* path, float* params_dev, void* stream);
 
 /* Copy G_hat (Eq. 15, after crop and DFT) for coarsest size m to out_dev, complex64
  * [nk][2m][2m]; builds it if needed.  HELM_ESTATE for an explicit U-Net. */

@@ -455,6 +455,7 @@ class Network:
         rc = restrict(rn)                                     # fixed R to I/2
         x0 = Var(np.stack([rc.real, rc.imag], axis=1))
         tp = Tape(self.params, record=record)
+        tp.x0, tp.r, tp.s_safe = x0, r, s_safe
         running = self.running if train else self.running
         kf = Var(kfeat)
         encs = encoder(tp, kf, train, running)
@@ -464,6 +465,7 @@ class Network:
         e = prolong(pc) * s[:, None, None]
         tp.out = p
         tp.scale = s
+        tp.e = e
         return e, tp
 
     def backward(self, tp: Tape, grad_e: np.ndarray):
@@ -473,6 +475,29 @@ class Network:
         tp.out.g = np.stack([gpc.real, gpc.imag], axis=1)
         tp.backward()
         return tp.grads
+
+    def input_gradient(self, tp: Tape, grad_e: np.ndarray) -> np.ndarray:
+        """dL/dRe r + i dL/dIm r after `backward(tp, grad_e)`, through every step of
+        e = s P(Net(R(r / s))), s = RMS(r) = sqrt(<r, r> / n) (n grid points per
+        sample, <a, b> = Re sum conj(a) b), the scale included:
+            u = r / s                 ->  dL/du = R^T dL/dx0 = P(dL/dx0) / 4
+            e = s q, q = P(Net(R u))  ->  dL/ds (direct) = <grad_e, q>
+            u = r / s                 ->  dL/dr = dL/du / s,  dL/ds -= <dL/du, r> / s^2
+            s = sqrt(<r, r> / n)      ->  dL/dr += dL/ds r / (n s)
+        A zero sample (s = 0) gets a zero gradient."""
+        gx = tp.x0.g
+        gu = prolong(gx[:, 0] + 1j * gx[:, 1]) / 4.0
+        r, s, e = tp.r, tp.scale, tp.e
+        B = r.shape[0]
+        n = r[0].size
+        out = np.zeros_like(r)
+        for b in range(B):
+            if not s[b] > 0:
+                continue
+            q = e[b] / s[b]
+            gs = np.real(np.vdot(grad_e[b], q)) - np.real(np.vdot(gu[b], r[b])) / s[b] ** 2
+            out[b] = gu[b] / s[b] + gs * r[b] / (n * s[b])
+        return out
 
 
 def fold_bn(params, running, name):

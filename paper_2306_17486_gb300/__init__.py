@@ -79,10 +79,11 @@ def mg_opts(levels=3, beta=0.5, omega_jacobi=0.8, coarse_iters=10, sl_includes_g
     return o
 
 
-def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1, cnn_every=1):
+def fgmres_opts(restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, reorth=1, cnn_every=1, fallback=True):
     o = FgmresOpts()
+    lib().helm_fgmres_opts_default(C.byref(o))
     o.restart, o.rtol, o.maxit, o.warmup_iters, o.reorth = restart, rtol, maxit, warmup_iters, reorth
-    o.cnn_every = cnn_every
+    o.cnn_every, o.fallback = cnn_every, int(fallback)
     return o
 
 
@@ -180,7 +181,8 @@ def slmg_vcycle_static(p: Problem, r: torch.Tensor, z: torch.Tensor | None = Non
 
 
 def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn=None, restart=10, rtol=1e-6,
-                 maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None, cnn_every=1):
+                 maxit=2000, warmup_iters=3, reorth=1, maxit_per_rhs: torch.Tensor | None = None, cnn_every=1,
+                 fallback=True):
     """Solve h^2 A x = b (b complex64 [B, ny, nx]); x complex128 (in: x0, out: solution).
     Returns (x, stats) with stats a numpy structured array (iters, status, rel_res_est,
     rel_res_true) per right-hand side."""
@@ -192,7 +194,7 @@ def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn
         raise HelmError(f"x has shape {tuple(x.shape)}, b {tuple(b.shape)}")
     stats = torch.zeros(B * STATS_DTYPE.itemsize, dtype=torch.uint8, device=b.device)
     ws = p.workspace(B, restart, cnn)
-    o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth, cnn_every)
+    o = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth, cnn_every, fallback)
     caps = None
     if maxit_per_rhs is not None:
         _batch_vec(maxit_per_rhs, B, torch.int32, "maxit_per_rhs", b.device)
@@ -418,15 +420,33 @@ class Cnn:
         self._train_p0 = probs[0]
         return e
 
-    def backward(self, p, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None) -> torch.Tensor:
+    def backward(self, p, grad_e: torch.Tensor, grad_params: torch.Tensor | None = None,
+                 r: torch.Tensor | None = None):
+        """Parameter gradient of the last training forward; with `r` (that forward's
+        input) also the input gradient: returns grad_params, or (grad_params, grad_r)."""
         p = p[0] if isinstance(p, (list, tuple)) else p
         B = _grid(p, grad_e, torch.complex64, "grad_e")
         g = torch.empty_like(self.params) if grad_params is None else grad_params
         _batch_vec(g, self.nparams, torch.float32, "grad_params", self.params.device)
+        gr = None
+        if r is not None:
+            if _grid(p, r, torch.complex64, "r") != B or r.shape != grad_e.shape:
+                raise HelmError("r must have grad_e's shape")
+            gr = torch.empty_like(r)
         ws = self.train_workspace(p, B, getattr(self, "_train_nprob", 1))
-        check(lib().helm_cnn_precond_backward(p.handle, self.handle, _ptr(grad_e), _ptr(g), B, _ptr(ws), ws.numel(),
-                                              _stream()), "helm_cnn_precond_backward")
-        return g
+        check(lib().helm_cnn_precond_backward(p.handle, self.handle, _ptr(r), _ptr(grad_e), _ptr(gr), _ptr(g), B,
+                                              _ptr(ws), ws.numel(), _stream()), "helm_cnn_precond_backward")
+        return g if r is None else (g, gr)
+
+    # ---- persistence ------------------------------------------------------------
+    def save(self, path: str):
+        """helm_cnn_save: parameters, BN statistics and the G_hat the handle holds."""
+        check(lib().helm_cnn_save(self.handle, str(path).encode(), _stream()), "helm_cnn_save")
+
+    def load(self, path: str):
+        """helm_cnn_load into this handle's parameter vector (same descriptor)."""
+        check(lib().helm_cnn_load(self.handle, str(path).encode(), _ptr(self.params), _stream()), "helm_cnn_load")
+        check(lib().helm_cnn_get_running(self.handle, _ptr(self.running), _stream()), "get_running")
 
 
 def mse_loss(e_pred: torch.Tensor, e_true: torch.Tensor, grad: bool = True):
@@ -462,15 +482,26 @@ class Adam:
 
 class CnnFunction(torch.autograd.Function):
     """torch.autograd wrapper around the training forward / backward kernels:
-    e = CnnFunction.apply(params, r, net, problem).  Gradients flow to `params`."""
+    e = CnnFunction.apply(params, r, net, problem), with `params` the network's own
+    parameter vector (net.params).  Gradients flow to `params` and, when r requires
+    one, to r (the library's input gradient, the RMS scale's dependence included)."""
 
     @staticmethod
     def forward(ctx, params, r, net, problem):
+        if params.data_ptr() != net.params.data_ptr():
+            raise HelmError("CnnFunction: params must be the network's parameter vector (net.params)")
         ctx.net, ctx.problem = net, problem
+        ctx.need_r = ctx.needs_input_grad[1]
+        if ctx.need_r:
+            ctx.save_for_backward(r)
         return net.forward_train(problem, r)
 
     @staticmethod
     def backward(ctx, grad_e):
+        if ctx.need_r:
+            (r,) = ctx.saved_tensors
+            g, gr = ctx.net.backward(ctx.problem, grad_e.contiguous(), r=r.contiguous())
+            return g, gr, None, None
         g = ctx.net.backward(ctx.problem, grad_e.contiguous())
         return g, None, None, None
 

@@ -26,7 +26,7 @@ class MgOpts(C.Structure):
 
 class FgmresOpts(C.Structure):
     _fields_ = [("restart", i32), ("rtol", f64), ("maxit", i32), ("warmup_iters", i32), ("reorth", i32),
-                ("cnn_every", i32)]
+                ("cnn_every", i32), ("fallback", i32)]
 
 
 class FgmresStats(C.Structure):
@@ -63,6 +63,8 @@ PROTOS = {
     "helm_profile_read": (i32, [i32, C.POINTER(C.c_char_p), C.POINTER(C.c_long), C.POINTER(f64)]),
     "helm_conv_bf16": (i32, [vp, i32, i32, i32, i32, vp, i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp, vp, sz,
                               vp]),
+    "helm_ib_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+    "helm_implicit_bf16": (i32, [vp, i32, i32, i32, vp, vp, vp]),
     "helm_cnn_create": (i32, [C.POINTER(CnnDesc), C.POINTER(vp)]),
     "helm_cnn_destroy": (i32, [vp]),
     "helm_cnn_num_params": (i32, [vp, C.POINTER(sz)]),
@@ -76,7 +78,9 @@ PROTOS = {
     "helm_cnn_get_ghat": (i32, [vp, i32, vp, vp]),
     "helm_cnn_apply": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp]),
     "helm_cnn_precond_apply": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
-    "helm_cnn_precond_backward": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
+    "helm_cnn_precond_backward": (i32, [vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
+    "helm_cnn_save": (i32, [vp, C.c_char_p, vp]),
+    "helm_cnn_load": (i32, [vp, C.c_char_p, vp, vp]),
     "helm_cnn_train_workspace_size": (i32, [vp, vp, i32, i32, C.POINTER(sz)]),
     "helm_cnn_train_forward": (i32, [C.POINTER(vp), i32, vp, vp, vp, i32, vp, sz, vp]),
     "helm_mse_loss": (i32, [vp, vp, C.c_long, i32, vp, vp, vp, vp]),

@@ -634,3 +634,17 @@ int launch_proj(const bf16* u, int B, int Nc, int C, const float* w, const float
 }
 
 }  // namespace helm
+
+extern "C" int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat, void* y, void* stream) {
+  using namespace helm;
+  if (!x || !ghat || !y || x == y || batch <= 0 || m <= 0 || c <= 0 || c % 2) {
+    set_error("helm_implicit_bf16: invalid argument (even channel count, distinct x and y)");
+    return HELM_EINVAL;
+  }
+  if (c % 8) {
+    set_error("helm_implicit_bf16: channels must be a multiple of 8 (NHWC groups of 8)");
+    return HELM_EINVAL;
+  }
+  return launch_implicit_bf16(static_cast<const bf16*>(x), batch, m, c, static_cast<const float2*>(ghat),
+                              static_cast<bf16*>(y), static_cast<cudaStream_t>(stream));
+}

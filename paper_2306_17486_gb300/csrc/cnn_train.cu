@@ -278,6 +278,136 @@ __global__ void k_conv_dgrad(ConvGeo g, const float* __restrict__ dz, const floa
   }
 }
 
+// the same for inputs with fewer than 8 channels (the network's 2-channel input):
+// thread per (pixel, channel)
+__global__ void k_conv_dgrad_narrow(ConvGeo g, const float* __restrict__ dz, const float* __restrict__ wp,
+                                    float* __restrict__ dX) {
+  const long total = static_cast<long>(g.B) * g.Hi * g.Wi * g.Ci;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int ci = static_cast<int>(i % g.Ci);
+    const long pix = i / g.Ci;
+    const int ix = static_cast<int>(pix % g.Wi), iy = static_cast<int>((pix / g.Wi) % g.Hi);
+    const int b = static_cast<int>(pix / (static_cast<long>(g.Wi) * g.Hi));
+    float acc = 0.f;
+    for (int tap = 0; tap < g.taps; ++tap) {
+      const int ty = g.taps == 1 ? 1 : tap / 3, tx = g.taps == 1 ? 1 : tap % 3;
+      const int dy = ty - 1, dx = tx - 1;
+      int oy, ox;
+      if (g.taps == 1) {
+        oy = iy;
+        ox = ix;
+      } else if (g.mode == HELM_CONV_S2) {
+        if ((iy - dy) & 1 || (ix - dx) & 1) continue;
+        oy = (iy - dy) >> 1;
+        ox = (ix - dx) >> 1;
+      } else if (g.mode == HELM_CONV_T2) {
+        oy = 2 * iy - dy;
+        ox = 2 * ix - dx;
+      } else {
+        oy = iy - dy;
+        ox = ix - dx;
+      }
+      if (oy < 0 || oy >= g.Ho || ox < 0 || ox >= g.Wo) continue;
+      const float* dzp = dz + ((static_cast<long>(b) * g.Ho + oy) * g.Wo + ox) * g.Co;
+      const float* wt = wp + static_cast<long>(tap) * g.Co * g.Ci + ci;
+      for (int co = 0; co < g.Co; ++co) acc = fmaf(wt[static_cast<long>(co) * g.Ci], dzp[co], acc);
+    }
+    dX[i] += acc;
+  }
+}
+
+// ---- input gradient of e = s P(Net(R(r / s))), s = RMS(r) ----------------------------
+// With x0 = R(r/s) and g0 = dL/dx0 (complex view of its two channels), the gradient is
+//   t = P(g0) / (4 s)                          (through u = r / s, R^T = P / 4)
+//   grad_r = t + r (<grad_e, e> - <t, r>) / (n s^2)
+// (<a, b> = Re sum conj(a) b over the n grid points); the second term is the scale's
+// dependence on r, fixed by e being positively homogeneous of degree 1 in r.
+// Stage 1: t at every fine point (bilinear P: even fine index = coarse value, odd =
+// mean of its two coarse neighbours, zero beyond the last coarse row / column).
+__global__ void k_gradr_t(const float* __restrict__ g0, int N, int B, const float* __restrict__ s,
+                          float2* __restrict__ t) {
+  const int Nc = N / 2;
+  const long total = static_cast<long>(B) * N * N;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(i / (static_cast<long>(N) * N));
+    const int y = static_cast<int>((i / N) % N), x = static_cast<int>(i % N);
+    const float* gb = g0 + static_cast<long>(b) * Nc * Nc * 2;
+    auto at = [&](int J, int K) -> float2 {
+      if (J >= Nc || K >= Nc) return make_float2(0.f, 0.f);
+      const float* q = gb + (static_cast<long>(J) * Nc + K) * 2;
+      return make_float2(q[0], q[1]);
+    };
+    const int J = y >> 1, K = x >> 1;
+    float2 v;
+    if (!(y & 1) && !(x & 1)) v = at(J, K);
+    else if (!(y & 1)) v = cscale(cadd(at(J, K), at(J, K + 1)), 0.5f);
+    else if (!(x & 1)) v = cscale(cadd(at(J, K), at(J + 1, K)), 0.5f);
+    else v = cscale(cadd(cadd(at(J, K), at(J, K + 1)), cadd(at(J + 1, K), at(J + 1, K + 1))), 0.25f);
+    const float sb = s[b];
+    t[i] = sb > 0.f ? cscale(v, 0.25f / sb) : make_float2(0.f, 0.f);
+  }
+}
+
+// Stage 2: per-block partial sums of <grad_e, e> and <t, r> per sample (FP64 across
+// threads, deterministic order)
+__global__ void k_gradr_dots(const float2* __restrict__ ge, const float2* __restrict__ e,
+                             const float2* __restrict__ t, const float2* __restrict__ r, long n, int nblk,
+                             double* __restrict__ part /*[B][nblk][2]*/) {
+  const int b = blockIdx.y;
+  const long chunk = (n + nblk - 1) / nblk;
+  const long p0 = blockIdx.x * chunk, p1 = min(p0 + chunk, n);
+  double a0 = 0.0, a1 = 0.0;
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const long q = static_cast<long>(b) * n + p;
+    const float2 g = ge[q], ev = e[q], tv = t[q], rv = r[q];
+    a0 += static_cast<double>(fmaf(g.x, ev.x, g.y * ev.y));
+    a1 += static_cast<double>(fmaf(tv.x, rv.x, tv.y * rv.y));
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  __shared__ double red[2][32];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a0;
+    red[1][threadIdx.x >> 5] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (blockDim.x >> 5); ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    part[(static_cast<long>(b) * nblk + blockIdx.x) * 2] = s0;
+    part[(static_cast<long>(b) * nblk + blockIdx.x) * 2 + 1] = s1;
+  }
+}
+
+// Stage 3: grad_r = t + c_b r, c_b = (<grad_e, e> - <t, r>) / (n s_b^2); zero where s_b = 0
+__global__ void k_gradr_fix(const double* __restrict__ part, int nblk, const float* __restrict__ s, long n,
+                            const float2* __restrict__ r, float2* __restrict__ gr) {
+  const int b = blockIdx.y;
+  __shared__ float cb;
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+      a0 += part[(static_cast<long>(b) * nblk + k) * 2];
+      a1 += part[(static_cast<long>(b) * nblk + k) * 2 + 1];
+    }
+    const double sb = s[b];
+    cb = sb > 0.0 ? static_cast<float>((a0 - a1) / (static_cast<double>(n) * sb * sb)) : 0.f;
+  }
+  __syncthreads();
+  const float c = cb;
+  for (long p = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; p < n;
+       p += static_cast<long>(gridDim.x) * blockDim.x) {
+    const long q = static_cast<long>(b) * n + p;
+    const float2 rv = r[q], tv = gr[q];
+    gr[q] = make_float2(fmaf(c, rv.x, tv.x), fmaf(c, rv.y, tv.y));
+  }
+}
+
 // dW partials: block (tap, TCO x TCI output tile, pixel chunk) -> [chunk][tap][co][ci].
 // 256 threads, each a (TCO/16) x (TCI/16) register tile; 32 pixels staged per pass
 // (the pixel's source index is computed once per pixel, shared by the whole tile).
@@ -761,7 +891,9 @@ struct TrainState {
   std::vector<float*> emean, eistd, smean, sistd;
   float *s, *inv;
   double* part;
+  float2* esave;   // the forward's output e, for the input gradient
   // backward
+  float* gx0;      // dL/dx0 of the network input (only when the input gradient is asked for)
   std::vector<float*> egrad, sgrad;  // dT per tensor
   float* dz;
   float* wpart;
@@ -806,6 +938,7 @@ static void carve_train(const helm_cnn* c, int I, int B, int nprob, Carve& cv, T
   T->s = cv.take<float>(B);
   T->inv = cv.take<float>(B);
   T->part = cv.take<double>(static_cast<size_t>(B) * 256 + 2 * 384 * kMaxChunks);
+  T->esave = cv.take<float2>(static_cast<size_t>(B) * I * I);
   if (with_backward) {
     size_t maxel = 0;
     auto grads = [&](const Plan& pl, std::vector<float*>& g) {
@@ -836,6 +969,7 @@ static void carve_train(const helm_cnn* c, int I, int B, int nprob, Carve& cv, T
     T->gghat = cv.take<float2>(static_cast<size_t>(nk) * n * n);
     T->gscr = cv.take<float2>(static_cast<size_t>(nk) * (n * n + n * n6 + n6 * n6));
     T->ppart = cv.take<float>(static_cast<size_t>(kMaxChunks) * (2 * 16 + 2));
+    T->gx0 = cv.take<float>(static_cast<size_t>(B) * (I / 2) * (I / 2) * 2);
   }
   T->overflow = cv.overflow;
 }
@@ -944,6 +1078,8 @@ int cnn_forward_train(helm_cnn* c, const helm_problem* const* probs, int nprob, 
   rc = launch_proj(static_cast<const bf16*>(T.sptr[T.u3]), B, I / 2, T.sol.t[T.u3].C, c->params_dev + pw.offset,
                    c->params_dev + pb.offset, T.s, e, st);
   if (rc) return rc;
+  HELM_CUDA(cudaMemcpyAsync(T.esave, e, static_cast<size_t>(B) * I * I * sizeof(float2), cudaMemcpyDeviceToDevice,
+                            st));
   c->enc_prob = nullptr;  // the cached evaluation-mode encodings are stale now
   c->dirty = true;        // running statistics moved: refold before the next inference
   c->train_nprob = nprob;
@@ -1041,8 +1177,14 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
     if (grad[L.in]) {
       const long nw = static_cast<long>(g.taps) * g.Co * g.Ci;
       HELM_LAUNCH("k_pack_dgrad_w", st, k_pack_dgrad_w<<<gridn(nw), 256, 0, st>>>(g, PP(c, L.wparam), T.wpart));
-      const long nin = static_cast<long>(in.B) * in.H * in.W * (in.C / 8);
-      HELM_LAUNCH("k_conv_dgrad", st, k_conv_dgrad<<<gridn(nin), 256, 0, st>>>(g, T.dz, T.wpart, grad[L.in]));
+      if (in.C % 8 == 0) {
+        const long nin = static_cast<long>(in.B) * in.H * in.W * (in.C / 8);
+        HELM_LAUNCH("k_conv_dgrad", st, k_conv_dgrad<<<gridn(nin), 256, 0, st>>>(g, T.dz, T.wpart, grad[L.in]));
+      } else {
+        const long nin = static_cast<long>(in.B) * in.H * in.W * in.C;
+        HELM_LAUNCH("k_conv_dgrad_narrow", st,
+                    k_conv_dgrad_narrow<<<gridn(nin), 256, 0, st>>>(g, T.dz, T.wpart, grad[L.in]));
+      }
     }
     const int nch = div_up(P, WG_PIX);
     if (static_cast<size_t>(nch) * g.taps * g.Co * g.Ci > T.wpart_elems) {
@@ -1071,8 +1213,8 @@ static int run_layers_backward(helm_cnn* c, const Plan& pl, const TrainState& T,
   return HELM_OK;
 }
 
-int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gparams, int B, Carve& cv,
-                 cudaStream_t st) {
+int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* r, const float2* ge, float2* grad_r,
+                 float* gparams, int B, Carve& cv, cudaStream_t st) {
   const int I = p->nx;
   if (c->train_nprob < 1) {
     set_error("cnn backward: no training forward to differentiate");
@@ -1084,6 +1226,7 @@ int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gp
     set_error("cnn backward: workspace too small");
     return HELM_EWORKSPACE;
   }
+  if (grad_r) T.sgrad[T.x0] = T.gx0;   // the network input's gradient is needed too
   // zero the activation gradients and the parameter gradients
   for (size_t i = 0; i < T.egrad.size(); ++i)
     if (T.egrad[i])
@@ -1115,6 +1258,17 @@ int cnn_backward(helm_cnn* c, const helm_problem* p, const float2* ge, float* gp
   // output-tensor gradients (aliased in carve_train), then the encoder runs backward
   int rc = run_layers_backward(c, T.sol, T, T.sptr, T.sraw, T.smean, T.sistd, T.sgrad, gparams, st);
   if (rc) return rc;
+  if (grad_r) {
+    const long n = static_cast<long>(I) * I;
+    const int nblk = std::max(1, std::min(128, div_up(n, 8192)));
+    HELM_LAUNCH("k_gradr_t", st, k_gradr_t<<<gridn(static_cast<long>(B) * n), 256, 0, st>>>(T.gx0, I, B, T.s, grad_r));
+    HELM_LAUNCH("k_gradr_dots", st,
+                k_gradr_dots<<<dim3(nblk, B), 256, 0, st>>>(ge, T.esave, grad_r, r, n, nblk, T.part));
+    HELM_LAUNCH("k_gradr_fix", st,
+                k_gradr_fix<<<dim3(std::min<long>(div_up(n, 256), 512), B), 256, 0, st>>>(T.part, nblk, T.s, n, r,
+                                                                                          grad_r));
+    HELM_CHECK_LAUNCH("input gradient");
+  }
   return run_layers_backward(c, T.enc, T, T.eptr, T.eraw, T.emean, T.eistd, T.egrad, gparams, st);
 }
 
@@ -1147,15 +1301,15 @@ int helm_cnn_train_forward(const helm_problem* const* probs, int nprob, helm_cnn
                                  static_cast<cudaStream_t>(stream));
 }
 
-int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* grad_e, float* grad_params, int batch,
-                              void* ws, size_t ws_bytes, void* stream) {
-  if (!p || !c || !grad_e || !grad_params || batch <= 0 || !ws) {
-    helm::set_error("helm_cnn_precond_backward: invalid argument");
+int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* r, const void* grad_e, void* grad_r,
+                              float* grad_params, int batch, void* ws, size_t ws_bytes, void* stream) {
+  if (!p || !c || !grad_e || !grad_params || batch <= 0 || !ws || (grad_r && (!r || r == grad_r))) {
+    helm::set_error("helm_cnn_precond_backward: invalid argument (grad_r needs the forward's input r, distinct)");
     return HELM_EINVAL;
   }
   helm::Carve cv(ws, ws_bytes);
-  return helm::cnn_backward(c, p, static_cast<const float2*>(grad_e), grad_params, batch, cv,
-                            static_cast<cudaStream_t>(stream));
+  return helm::cnn_backward(c, p, static_cast<const float2*>(r), static_cast<const float2*>(grad_e),
+                            static_cast<float2*>(grad_r), grad_params, batch, cv, static_cast<cudaStream_t>(stream));
 }
 
 int helm_mse_loss(const void* e_pred, const void* e_true, long n, int batch, double* loss_dev, void* grad,

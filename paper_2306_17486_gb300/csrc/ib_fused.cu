@@ -354,3 +354,44 @@ int ib_fused(const IbLaunch& l, cudaStream_t st) {
 }
 
 }  // namespace helm
+
+extern "C" int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const float* w_exp, const float* bn0,
+                            const float* w_dw, const float* bn1, const float* w_proj, const float* bn2, void* y,
+                            void* ws, size_t ws_bytes, void* stream) {
+  using namespace helm;
+  if (!x || !w_exp || !bn0 || !w_dw || !bn1 || !w_proj || !bn2 || !y || x == y || batch <= 0 || h <= 0 || w <= 0) {
+    set_error("helm_ib_bf16: invalid argument (x and y must be distinct device buffers)");
+    return HELM_EINVAL;
+  }
+  if (c != 16 && c != 32 && c != 64) {
+    set_error("helm_ib_bf16: %d channels (kernels exist for 16, 32, 64)", c);
+    return HELM_EINVAL;
+  }
+  const int E = 6 * c;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve cv(ws, ws_bytes);
+  bf16* we = cv.take<bf16>(static_cast<size_t>(conv_cs(c)) * E);
+  bf16* wp = cv.take<bf16>(static_cast<size_t>(conv_cs(E)) * c);
+  if (cv.overflow || !ws) {
+    set_error("helm_ib_bf16: workspace too small (need %zu bytes)", cv.off);
+    return HELM_EWORKSPACE;
+  }
+  int rc = pack_conv_weights(w_exp, c, E, 1, 0, we, st);
+  if (!rc) rc = pack_conv_weights(w_proj, E, c, 1, 0, wp, st);
+  if (rc) return rc;
+  IbLaunch l;
+  l.x = static_cast<const bf16*>(x);
+  l.B = batch;
+  l.H = h;
+  l.W = w;
+  l.C = c;
+  l.expansion = 6;
+  l.we = we;
+  l.wp = wp;
+  l.wdw = w_dw;
+  l.bn0 = bn0;
+  l.bn1 = bn1;
+  l.bn2 = bn2;
+  l.y = static_cast<bf16*>(y);
+  return ib_fused(l, st);
+}

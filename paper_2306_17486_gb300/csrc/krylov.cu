@@ -57,7 +57,8 @@ struct Solver {
   double* prev;        // [B] true relative residual at the previous restart
   int* fb;             // [B] 1: this RHS fell back to the plain V-cycle preconditioner
   int* sel;            // [B] indices of the RHS the network runs on this cycle
-  int use_cnn;         // the composed preconditioner is in use (fallback test active)
+  int use_cnn;         // the composed preconditioner is in use
+  int allow_fb;        // a RHS may fall back to the plain V-cycle (stall or non-finite step)
 };
 
 // ---- streaming kernels ----------------------------------------------------------
@@ -235,16 +236,24 @@ __device__ void givens_step(Solver S, int b, int j, const double2* hc, double hn
   double2* sn = S.sn + static_cast<long>(b) * S.m;
   double2* g = S.g + static_cast<long>(b) * MAXV;
   bool ok = isfinite(hn);
-  for (int i = 0; i <= j; ++i) {
-    col[i] = hc[i];
-    ok = ok && finite2(hc[i]);
-  }
+  for (int i = 0; i <= j; ++i) ok = ok && finite2(hc[i]);
   if (!ok) {
+    if (S.use_cnn && S.allow_fb && !S.fb[b]) {
+      // a non-finite column with the learned preconditioner in use: discard this step
+      // (the cycle keeps its j finite steps, x is updated with them at the restart) and
+      // hand the RHS to the plain V-cycle for the rest of its solve
+      S.fb[b] = 1;
+      S.iters[b] += 1;
+      S.kcyc[b] = j;
+      S.cyc[b] = 0;   // the restart residual decides CONVERGED / MAXIT as usual
+      return;
+    }
     S.status[b] = HELM_STATUS_NONFINITE;
     S.cyc[b] = 0;
     S.active[b] = 0;
     return;
   }
+  for (int i = 0; i <= j; ++i) col[i] = hc[i];
   for (int i = 0; i < j; ++i) {
     double2 a = col[i], c = col[i + 1];
     col[i] = zadd(zscale(a, cs[i]), zmul(sn[i], c));
@@ -395,7 +404,7 @@ __global__ void k_fin_restart(Solver S, double tol) {
     } else {
       // a cycle with the learned preconditioner that failed to reduce the residual
       // hands this RHS to the plain SL V-cycle for the rest of the solve
-      if (S.use_cnn && !S.fb[b] && S.prev[b] > 0.0 && rel > 0.95 * S.prev[b]) S.fb[b] = 1;
+      if (S.use_cnn && S.allow_fb && !S.fb[b] && S.prev[b] > 0.0 && rel > 0.95 * S.prev[b]) S.fb[b] = 1;
       S.prev[b] = rel;
       S.cyc[b] = 1;
       S.inv[b] = static_cast<float>(1.0 / beta);
@@ -545,6 +554,7 @@ void helm_fgmres_opts_default(helm_fgmres_opts* o) {
   o->warmup_iters = 3;
   o->reorth = 1;
   o->cnn_every = 1;
+  o->fallback = 1;
 }
 
 int helm_workspace_size(const helm_problem* p, const helm_cnn* cnn, int batch, int restart, size_t* bytes) {
@@ -592,6 +602,7 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
   const long vstride = static_cast<long>(B) * n;
   const int m = o.restart;
   S.use_cnn = cnn != nullptr ? 1 : 0;
+  S.allow_fb = o.fallback ? 1 : 0;
   dim3 gs(S.nblk, B);
   int rc;
 

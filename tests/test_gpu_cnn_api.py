@@ -1,0 +1,210 @@
+"""GPU tests of the network's C-ABI surface beyond the forward pass: the input gradient
+of helm_cnn_precond_backward against the oracle's chain rule, the torch.autograd
+wrapper, saving and loading a network (Section 4.2: G_hat is stored with it), the
+FGMRES fallback option, and the trained network's iteration count on one right-hand
+side of the 576^2 workload against the oracle's own count."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import cnn as ocnn
+from oracle import helmholtz as ohz
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz")
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2306_17486_gb300 as h
+    return h
+
+
+def _bf(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+
+
+def _net_and_problem(helm, I=64, seed=21, gamma0=0.05):
+    P = synth.random_params(ocnn.param_spec(16), seed=seed, bn_jitter=0.2)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn()
+    net.load_dict(Pq)
+    abl = I // 8
+    kappa = synth.grf_kappa(I - 2 * abl, abl, 6.0, 3).astype(np.float32).astype(np.float64)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(kappa, dtype=torch.float32, device="cuda"), abl, oh, gamma0=gamma0, levels=3)
+    op = ohz.Problem(kappa, abl, omega_h=oh, gamma0=gamma0)
+    kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
+    return net, Pq, p, kf
+
+
+def test_input_gradient_matches_oracle(helm):
+    """grad_r of e = s Net(r / s): the GPU (BF16 activations, the closed form of the
+    scale term) against the oracle's step-by-step chain rule, itself pinned by central
+    differences.  Bound as for the parameter gradients: relative 2-norm 10 %, cosine
+    0.99; Euler's identity <grad_r, r> = <grad_e, e> within 2 % (the GPU's e is the
+    BF16 network's output)."""
+    I, B = 64, 2
+    net, Pq, p, kf = _net_and_problem(helm, I)
+    r = synth.random_complex((B, I, I), 5).astype(np.complex64).astype(np.complex128)
+    r[1] *= 3.0                                  # samples of different scale
+    et = (0.3 * synth.random_complex((B, I, I), 6)).astype(np.complex64).astype(np.complex128)
+    rg = torch.tensor(r, dtype=torch.complex64, device="cuda")
+    eg = net.forward_train(p, rg)
+    _, ge = helm.mse_loss(eg, torch.tensor(et, dtype=torch.complex64, device="cuda"))
+    g1, gr = net.backward(p, ge, r=rg)
+    g0 = net.backward(p, ge)                     # without the input gradient: same parameter gradient
+    assert torch.equal(g0, g1)
+    on = ocnn.Network(Pq, None, c0=16)
+    from oracle.training import mse_loss as omse
+    e_ref, tp = on.forward(r, kf, train=True, skip=True, record=True)
+    _, g_e = omse(e_ref, et)
+    on.backward(tp, g_e)
+    ref = on.input_gradient(tp, g_e)
+    a = gr.cpu().numpy()
+    for b in range(B):
+        rel = np.linalg.norm(a[b] - ref[b]) / np.linalg.norm(ref[b])
+        cos = np.real(np.vdot(a[b], ref[b])) / (np.linalg.norm(a[b]) * np.linalg.norm(ref[b]))
+        assert rel < 0.1 and cos > 0.99, (b, rel, cos)
+        lhs = np.real(np.vdot(a[b], r[b]))
+        rhs = np.real(np.vdot(ge[b].cpu().numpy(), eg[b].cpu().numpy()))
+        assert abs(lhs - rhs) <= 2e-2 * abs(rhs), (b, lhs, rhs)
+    # the input gradient needs the forward's input
+    with pytest.raises(helm.HelmError):
+        helm._lib.check(helm.lib().helm_cnn_precond_backward(p.handle, net.handle, None, helm._ptr(ge),
+                                                             helm._ptr(torch.empty_like(ge)), helm._ptr(g0), B,
+                                                             helm._ptr(net._tws), net._tws.numel(),
+                                                             helm._stream()), "backward")
+
+
+def test_autograd_function_matches_the_library_backward(helm):
+    """CnnFunction: torch.autograd through the library's training forward and backward
+    gives exactly the library's parameter and input gradients."""
+    I, B = 64, 2
+    net, _, p, _ = _net_and_problem(helm, I, seed=23)
+    r = torch.tensor(synth.random_complex((B, I, I), 7), dtype=torch.complex64, device="cuda")
+    et = torch.tensor(0.3 * synth.random_complex((B, I, I), 8), dtype=torch.complex64, device="cuda")
+    params = net.params.requires_grad_(True)
+    rr = r.clone().requires_grad_(True)
+    e = helm.CnnFunction.apply(params, rr, net, p)
+    loss = (e - et).abs().pow(2).sum() / B          # Eq. (16)
+    loss.backward()
+    e2 = net.forward_train(p, r)
+    _, ge = helm.mse_loss(e2, et)
+    g_ref, gr_ref = net.backward(p, ge, r=r)
+    assert torch.equal(e.detach(), e2)
+    # torch's own gradient of the loss w.r.t. e is 2 (e - et) / B, the library's mse
+    # kernel computes the same in FP32 with possibly different rounding
+    assert torch.allclose(params.grad, g_ref, rtol=1e-4, atol=1e-6 * g_ref.abs().max().item())
+    assert torch.allclose(rr.grad, gr_ref, rtol=1e-4, atol=1e-6 * gr_ref.abs().max().item())
+    params.requires_grad_(False)
+
+
+def test_save_load_roundtrip_is_bitwise(helm, tmp_path):
+    """helm_cnn_save / helm_cnn_load: parameters, BN statistics, the stored G_hat and the
+    network's output are bit-identical after a round trip; a file of another network
+    or a damaged file is rejected and leaves the handle as it was."""
+    from paper_2306_17486_gb300 import train as T
+    I = 128
+    net = helm.Cnn(skip_threshold=256)
+    T.load_weights(net, WEIGHTS)
+    abl = 16
+    kap = synth.grf_kappa(I - 2 * abl, abl, 8.0, 5)
+    p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device="cuda"), abl, 2 * np.pi / 10 / kap.max(),
+                     levels=3)
+    net.set_problem(p)
+    r = torch.tensor(synth.random_complex((3, I, I), 2), dtype=torch.complex64, device="cuda")
+    e0 = net.apply(p, r)
+    m = I // 8
+    gh0 = net.ghat(m)
+    path = str(tmp_path / "net.helmcnn")
+    net.save(path)
+    net2 = helm.Cnn(skip_threshold=256)
+    net2.load(path)
+    assert torch.equal(net2.params, net.params)
+    assert torch.equal(net2.running, net.running)
+    assert torch.equal(net2.ghat(m), gh0)
+    net2.set_problem(p)
+    assert torch.equal(net2.apply(p, r), e0)
+    # another descriptor: rejected, nothing changed
+    other = helm.Cnn(skip_threshold=512)
+    before = other.params.clone()
+    with pytest.raises(helm.HelmError, match="another descriptor"):
+        other.load(path)
+    assert torch.equal(other.params, before)
+    # a truncated file fails its size / hash check
+    raw = open(path, "rb").read()
+    bad = str(tmp_path / "bad.helmcnn")
+    open(bad, "wb").write(raw[:-100])
+    with pytest.raises(helm.HelmError, match="not a complete network file"):
+        net2.load(bad)
+    flipped = bytearray(raw)
+    flipped[len(raw) // 2] ^= 1
+    open(bad, "wb").write(bytes(flipped))
+    with pytest.raises(helm.HelmError, match="not a complete network file"):
+        net2.load(bad)
+
+
+def test_nonfinite_network_output_falls_back_to_the_vcycle(helm):
+    """A network whose output is not finite (here a corrupted weight): with the fallback
+    on, the step that met it is discarded and the RHS continues with the plain V-cycle
+    to convergence (true FP64 residual); with it off the RHS ends NONFINITE."""
+    from paper_2306_17486_gb300 import train as T
+    I, abl, B = 96, 16, 3
+    net = helm.Cnn(skip_threshold=256)
+    T.load_weights(net, WEIGHTS)
+    idx = dict((n, (s, o)) for n, s, o in net.spec)["s.l2.conv.w"][1]
+    bad = net.params.clone()
+    bad[idx + 5] = float("nan")
+    net.set_params(bad)
+    kap = synth.grf_kappa(I - 2 * abl, abl, 8.0, 6)
+    p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device="cuda"), abl, 2 * np.pi / 10 / kap.max(),
+                     levels=3)
+    net.set_problem(p)
+    b = synth.random_point_sources(I, abl, B, seed=4)
+    bg = torch.tensor(b, dtype=torch.complex64, device="cuda")
+    _, st_mg = helm.fgmres_solve(p, bg)
+    x, st = helm.fgmres_solve(p, bg, cnn=net)
+    op = ohz.Problem(kap.astype(np.float32).astype(np.float64), abl, omega_h=2 * np.pi / 10 / kap.max())
+    xs = x.cpu().numpy()
+    for i in range(B):
+        assert st["status"][i] == 1, st
+        assert np.linalg.norm(b[i] - op.A(xs[i])) <= 1e-6 * np.linalg.norm(b[i])
+        # the three warm-up steps, the discarded network step, then the V-cycle alone
+        assert st["iters"][i] <= st_mg["iters"][i] + 12, (st, st_mg)
+    _, st_off = helm.fgmres_solve(p, bg, cnn=net, fallback=False)
+    assert (st_off["status"] == 3).all(), st_off
+    assert helm.device_errors() == 0
+
+
+def test_trained_network_iteration_count_matches_the_oracle(helm):
+    """The committed network on right-hand side 0 of slowness model 10 of the 576^2
+    workload, FGMRES(10) with the composed preconditioner on every step (the paper's
+    schedule) after a 3-step V-cycle warm-up, to 1e-6, with the per-RHS fallback off
+    (the oracle has none): the GPU's BF16 network and FP32 Krylov vectors must reach
+    the oracle's FP64 iteration count (stored by tests/golden/make_oracle_iterations.py)
+    within 10 %."""
+    from paper_2306_17486_gb300 import train as T
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_iterations_576.json")))
+    n_oracle = gold["cnn_mg"]["results"][0]["iterations"]
+    net = helm.Cnn(skip_threshold=256)
+    T.load_weights(net, WEIGHTS)
+    kap = synth.grf_kappa(512, 32, 8.0, seed=10)
+    p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device="cuda"), 32, 2 * np.pi / 10 / kap.max(),
+                     levels=4)
+    net.set_problem(p)
+    b = synth.random_point_sources(576, 32, 64, seed=1000)[:1]
+    x, st = helm.fgmres_solve(p, torch.tensor(b, dtype=torch.complex64, device="cuda"), cnn=net, restart=10,
+                              rtol=1e-6, maxit=2000, warmup_iters=3, cnn_every=1, fallback=False)
+    assert st["status"][0] == 1, st
+    assert abs(int(st["iters"][0]) - n_oracle) <= 0.1 * n_oracle, (int(st["iters"][0]), n_oracle)

@@ -242,3 +242,36 @@ def test_mse_loss_gradient_and_adam_first_step():
     tr.adam_step(params, grads, {}, lr=GOLD["adam_lr"]["value"])
     step = params["w"] - np.array([1.0, -2.0, 0.5])
     assert np.allclose(step, -1e-3 * np.sign(grads["w"]), rtol=1e-4)
+
+
+@pytest.mark.parametrize("train", [True, False], ids=["train", "eval"])
+def test_network_input_gradient_matches_central_differences(train):
+    """dL/dr of e = s Net(r / s), s = RMS(r), with the scale's own dependence on r:
+    directional derivatives along random complex directions against 4-point central
+    differences (FP64), relative 1e-6; and Euler's identity <dL/dr, r> = <dL/de, e>,
+    which holds because e is positively homogeneous of degree 1 in r."""
+    net, P, kf, r, et = _setup(B=2)
+    e, tp = net.forward(r, kf, train=train, skip=True, record=True)
+    L, ge = tr.mse_loss(e, et)
+    net.backward(tp, ge)
+    gr = net.input_gradient(tp, ge)
+    assert np.all(np.isfinite(gr))
+    rng = np.random.default_rng(11)
+
+    def loss_at(rr):
+        running = {k: (v[0].copy(), v[1].copy()) for k, v in net.running.items()}
+        saved = net.running
+        net.running = running
+        ee, _ = net.forward(rr, kf, train=train, skip=True)
+        net.running = saved
+        return tr.mse_loss(ee, et)[0]
+
+    for _ in range(3):
+        d = rng.standard_normal(r.shape) + 1j * rng.standard_normal(r.shape)
+        h = 1e-4 * np.abs(r).max()
+        vals = [loss_at(r + c * h * d) for c in (2, 1, -1, -2)]
+        fd = (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * h)
+        an = float(np.real(np.vdot(gr, d)))
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-12 * abs(L)), (fd, an)
+    euler = float(np.real(np.vdot(gr, r)))
+    assert abs(euler - float(np.real(np.vdot(ge, e)))) <= 1e-10 * np.abs(gr).sum() * np.abs(r).max()
