@@ -302,6 +302,15 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
                                                                            static_cast<int>(c->bns.size()), 1e-5f,
                                                                            c->fold));
     HELM_CHECK_LAUNCH("k_fold_bn");
+    // the inverted bottlenecks' 1x1 weights with BN0 / BN2 folded in (evaluation mode)
+    for (const auto& kv : c->wfold_off) {
+      const ParamInfo& pi = c->params[kv.first];
+      const bool expw = pi.name.find(".exp.w") != std::string::npos;
+      const std::string bn = pi.name.substr(0, pi.name.rfind('.', pi.name.size() - 3)) + (expw ? ".bn0" : ".bn2");
+      const int rc = pack_ib_folded(c->params_dev + pi.offset, c->fold + c->bns[c->bidx.at(bn)].roff, pi.shape[1],
+                                    pi.shape[0], expw ? 0 : 1, c->wfold + kv.second, st);
+      if (rc) return rc;
+    }
     HELM_CUDA(cudaStreamSynchronize(st));  // dmeta is scratch reused below
     for (auto& kv : c->ghat) cudaFree(kv.second);
     c->ghat.clear();
@@ -384,6 +393,8 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
       il.bn0 = fold;
       il.bn1 = c->fold + c->bns[L.bn_dw].roff;
       il.bn2 = c->fold + c->bns[L.bn_proj].roff;
+      il.wef = c->wfold + c->wfold_off.at(L.wparam);
+      il.wpf = c->wfold + c->wfold_off.at(L.wp_proj);
       il.y = static_cast<__nv_bfloat16*>(ptr[L.out]);
       rc = ib_fused(il, st);
     } else if (L.kind == L_DW) {
@@ -547,7 +558,16 @@ int helm_cnn_create(const helm_cnn_desc* desc, helm_cnn** out) {
   size_t wp = 0;
   for (const ParamInfo& pi : c->params) wp += packed_elems(c, pi);
   c->wpk_elems = wp;
+  size_t wf = 0;
+  for (size_t i = 0; i < c->params.size(); ++i) {
+    const ParamInfo& pi = c->params[i];
+    if (pi.name.find(".ib.exp.w") == std::string::npos && pi.name.find(".ib.proj.w") == std::string::npos) continue;
+    c->wfold_off[static_cast<int>(i)] = wf;
+    wf += ib_folded_elems(pi.shape[1], pi.shape[0]);
+  }
+  c->wfold_elems = wf;
   if (cudaMalloc(&c->wpk, wp * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&c->wfold, wf * sizeof(__nv_bfloat16)) != cudaSuccess ||
       cudaMalloc(&c->running, c->nrunning * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->fold, c->nrunning * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->gscratch, 4096 * sizeof(float2)) != cudaSuccess) {
@@ -572,6 +592,7 @@ int helm_cnn_create(const helm_cnn_desc* desc, helm_cnn** out) {
 int helm_cnn_destroy(helm_cnn* c) {
   if (!c) return HELM_OK;
   cudaFree(c->wpk);
+  cudaFree(c->wfold);
   cudaFree(c->running);
   cudaFree(c->fold);
   cudaFree(c->gscratch);

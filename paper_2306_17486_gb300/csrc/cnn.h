@@ -38,9 +38,19 @@ struct IbLaunch {
   const float* bn0 = nullptr;          // folded BN (scale | shift) after each stage
   const float* bn1 = nullptr;
   const float* bn2 = nullptr;
+  // 16 and 32 channels: the 1x1 weights with BN0 / BN2 folded in (pack_ib_folded)
+  const __nv_bfloat16* wef = nullptr;  // [C/8 + 2][6C][8]
+  const void* wpf = nullptr;           // [6C/8 + 2][C][8], FP16
   __nv_bfloat16* y = nullptr;
 };
 int ib_fused(const IbLaunch& l, cudaStream_t st);
+int ib_strip(const IbLaunch& l, cudaStream_t st);   // C = 16, 32 (ib_strip.cu)
+// 1x1 weights w [Co][Ci] with a folded BatchNorm (fold: scale [Co] then shift [Co]) for
+// the strip kernel: [Ci/8 + 2][Co][8] in BF16 (fp16 = 0) or FP16 (fp16 = 1), the last two
+// 8-channel groups holding the shift (channel 0 for BF16, 1 for FP16) and zeros; Ci a
+// multiple of 16
+size_t ib_folded_elems(int Ci, int Co);
+int pack_ib_folded(const float* w, const float* fold, int Ci, int Co, int fp16, void* out, cudaStream_t st);
 int pack_conv_weights(const float* w, int Ci, int Co, int taps, int transposed, __nv_bfloat16* out, cudaStream_t st);
 
 }  // namespace helm

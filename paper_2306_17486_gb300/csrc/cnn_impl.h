@@ -73,6 +73,10 @@ struct helm_cnn {
   float* fold = nullptr;              // owned: folded BN scale/shift [same layout as running]
   __nv_bfloat16* wpk = nullptr;       // owned: packed conv weights
   size_t wpk_elems = 0;
+  __nv_bfloat16* wfold = nullptr;     // owned: inverted-bottleneck 1x1 weights with BN folded in
+                                      // (expansion BF16, projection FP16 bits)
+  size_t wfold_elems = 0;
+  std::map<int, size_t> wfold_off;    // parameter index -> element offset in wfold
   std::map<int, float2*> ghat;        // owned: Green's function per coarsest size m
   float2* gscratch = nullptr;
   size_t gscratch_elems = 0;

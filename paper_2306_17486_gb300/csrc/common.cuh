@@ -122,12 +122,45 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Bounded wait that lets the waiting thread sleep: each try_wait may suspend the thread
+// for up to `ns` nanoseconds until the phase completes, instead of spinning on issue
+// slots that the working warps of the SM need.  At most HELM_SLEEP_WAIT_LIMIT tries.
+#define HELM_SLEEP_WAIT_LIMIT (1u << 16)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, unsigned flag) {
+  for (uint32_t it = 0; it < HELM_SLEEP_WAIT_LIMIT; ++it) {
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+  }
+  atomicOr(&g_helm_device_error, flag);
+  return false;
+}
+
 // 3-D tiled TMA load global -> shared, completion signalled on `bar`.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 4-D tiled TMA load global -> shared, completion signalled on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -151,6 +184,11 @@ namespace helm {
 // Tensor map over a complex64 batch [nb][ny][nx] (viewed as float32 pairs), box of
 // box_w complex x box_h rows x 1 batch item, zero fill outside the tensor.
 int make_c64_map(CUtensorMap* out, const void* base, int nx, int ny, int nb, int box_w, int box_h);
+
+// Tensor map over one 8-channel group of a BF16 NHWC tensor [nb][H][W][C]: `base` points
+// at channel 8g of pixel 0; dims (8 channels, W, H, nb), box 8 x box_w x box_h x 1, zero
+// fill outside the tensor.  A box lands in shared memory as box_h x box_w pixels of 16 B.
+int make_bf16_nhwc_map(CUtensorMap* out, const void* base, int C, int W, int H, int B, int box_w, int box_h);
 
 inline int div_up(long a, long b) { return static_cast<int>((a + b - 1) / b); }
 

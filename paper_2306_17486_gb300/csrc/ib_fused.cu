@@ -343,6 +343,7 @@ int ib_fused(const IbLaunch& l, cudaStream_t st) {
     set_error("fused inverted bottleneck: expansion %d (kernels exist for 6)", l.expansion);
     return HELM_EINVAL;
   }
+  if ((l.C == 16 || l.C == 32) && l.wef && l.wpf) return ib_strip(l, st);   // the row-sweeping strip kernel
   switch (l.C) {
     case 16: return launch_ib_t<16>(a, st);
     case 32: return launch_ib_t<32>(a, st);
@@ -372,12 +373,16 @@ extern "C" int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const
   Carve cv(ws, ws_bytes);
   bf16* we = cv.take<bf16>(static_cast<size_t>(conv_cs(c)) * E);
   bf16* wp = cv.take<bf16>(static_cast<size_t>(conv_cs(E)) * c);
+  bf16* wef = cv.take<bf16>(ib_folded_elems(c, E));
+  bf16* wpf = cv.take<bf16>(ib_folded_elems(E, c));
   if (cv.overflow || !ws) {
     set_error("helm_ib_bf16: workspace too small (need %zu bytes)", cv.off);
     return HELM_EWORKSPACE;
   }
   int rc = pack_conv_weights(w_exp, c, E, 1, 0, we, st);
   if (!rc) rc = pack_conv_weights(w_proj, E, c, 1, 0, wp, st);
+  if (!rc && c != 64) rc = pack_ib_folded(w_exp, bn0, c, E, 0, wef, st);
+  if (!rc && c != 64) rc = pack_ib_folded(w_proj, bn2, E, c, 1, wpf, st);
   if (rc) return rc;
   IbLaunch l;
   l.x = static_cast<const bf16*>(x);
@@ -392,6 +397,8 @@ extern "C" int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const
   l.bn0 = bn0;
   l.bn1 = bn1;
   l.bn2 = bn2;
+  l.wef = c != 64 ? wef : nullptr;
+  l.wpf = c != 64 ? wpf : nullptr;
   l.y = static_cast<bf16*>(y);
   return ib_fused(l, st);
 }

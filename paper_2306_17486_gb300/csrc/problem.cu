@@ -80,6 +80,33 @@ int make_c64_map(CUtensorMap* out, const void* base, int nx, int ny, int nb, int
   return HELM_OK;
 }
 
+int make_bf16_nhwc_map(CUtensorMap* out, const void* base, int C, int W, int H, int B, int box_w, int box_h) {
+  PFN_encodeTiled enc = get_encode();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return HELM_ECUDA;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || C % 8 || box_w < 1 || box_w > 256 || box_h < 1 ||
+      box_h > 256) {
+    set_error("TMA map: base must be 16-byte aligned, channels a multiple of 8, box sides in [1, 256]");
+    return HELM_EINVAL;
+  }
+  cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H), static_cast<cuuint64_t>(B)};
+  cuuint64_t strides[3] = {static_cast<cuuint64_t>(C) * 2, static_cast<cuuint64_t>(W) * C * 2,
+                           static_cast<cuuint64_t>(H) * W * C * 2};
+  cuuint32_t box[4] = {8, static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a BF16 NHWC map C=%d W=%d H=%d B=%d box=%dx%d",
+              static_cast<int>(r), C, W, H, B, box_w, box_h);
+    return HELM_ECUDA;
+  }
+  return HELM_OK;
+}
+
 }  // namespace helm
 
 // --- setup kernels -----------------------------------------------------------------

@@ -8,17 +8,26 @@ at the benchmark's shape.
 * The network forward at I = 576 with the layer plan the benchmark runs (coarsest
   level I/16, batch 8, the persistent kernels wrapping over their segments).
 
-Per-element bounds follow the kernels' arithmetic (u16 = 2^-11 for FP16, ub = 2^-8
-for the BF16 rounding of a stored activation, doubled for margin):
-* bottleneck: the FP16 expanded activations and FP16 row sums of the depthwise stage
-  perturb its output by at most 3 u16 sum |w_dw||h| (h the expanded activation);
-  the depthwise output is stored in BF16 (ub |a|), so each projection input a_k is off
-  by at most ub (|a_k| + |s1_k| D_k), D_k = sum |w_dw||h|; the projection sums these
-  with |w_p|, BN2 scales by |s2|, and the output is rounded to BF16:
-      |y - y_ref| <= ub |y_ref| + ub |s2| sum_k |w_p| (|a_k| + |s1_k| D_k);
+Per-element bounds follow the kernels' arithmetic, with u = 2^-11 (FP16 unit roundoff),
+then doubled for margin:
+* bottleneck (16 and 32 channels: expanded activations, depthwise sums of 9 products,
+  both softplus evaluations and the projection's operands in FP16; 64 channels: FP32
+  softplus, FP32 sums of FP16 row sums and a BF16 projection operand, inside the same
+  bound).  A softplus evaluated in FP16 as
+  max(x, 0) + e q(e), e = 2^(-|x| log2 e), is off by at most
+      u (|s| + (2|x| + 6) (s - max(x, 0)))          (s = softplus(x))
+  (input and product roundings, the exp2 unit's 2u, the polynomial's evaluation); the
+  expanded activation h carries that error dh; the depthwise output d = sum w'h (w' the
+  FP16 weights times BN1's scale) adds 10 u sum|w'||h| for its FP16 accumulation and
+  weight rounding, and the BN1 shift u (|b1| + |v|); the second softplus adds its own
+  error and the BF16 rounding of a (4u |a|); the projection and BN2 pass sum|w_p||da|
+  times |s2| on, and the output is rounded to BF16 (2^-9 |y|).  At 16 and 32 channels
+  BN0 and BN2 run inside the tensor-core products with BF16(scale x w) and BF16(shift):
+  that adds 2^-9 (sum |s0 w||x| + |b0|) to the pre-activation (times the softplus slope
+  for h) and 2^-9 (sum |s2 w_p||a| + |b2|) to the projection;
 * implicit layer: four dense DFT stages of length 2m in FP32, each adding at most
   2m eps32 of the magnitude bound max|G_hat| sum|x|, then BF16 rounding:
-      |y - y_ref| <= ub |y_ref| + 4 (2m) 2^-24 max|G_hat| sum|x|.
+      |y - y_ref| <= 2^-8 |y_ref| + 4 (2m) 2^-24 max|G_hat| sum|x|.
 """
 import os
 
@@ -31,6 +40,7 @@ import synth
 from oracle import cnn as ocnn
 from oracle import helmholtz as ohz
 from oracle import implicit as oimp
+from oracle import multigrid as omg
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -86,12 +96,31 @@ def test_fused_inverted_bottleneck_matches_oracle_per_element(helm, C, B, H, W):
     # the same block through the oracle's own composition (checks the staging above)
     y_ib = ocnn.inverted_bottleneck(ocnn.Tape(P, record=False), ocnn.Var(x), "ib", False, running).a
     assert np.array_equal(y_ib, y_ref)
-    # magnitude terms of the bound
-    Dk = ocnn.depthwise3x3(ocnn.Tape({"w": np.abs(w_dw)}, record=False), ocnn.Var(np.abs(h.a)), "w").a
-    s1 = np.abs(P["ib.bn1.g"])[None, :, None, None]
+    # error propagation of the bound (module docstring)
+    u = 2.0 ** -11
+
+    def sp_err(xv, sv):
+        return u * (np.abs(sv) + (2 * np.abs(xv) + 6) * (sv - np.maximum(xv, 0.0)))
+
+    x0 = ocnn.batchnorm(ocnn.Tape(P, record=False), ocnn.conv1x1(ocnn.Tape(P, record=False), ocnn.Var(x), "ib.exp.w"),
+                        "ib.bn0", False, running).a
+    # 16 and 32 channels: BN0 runs inside the MMA with BF16(scale * w) and BF16(shift)
+    from scipy.special import expit
+    dx0 = 2.0 ** -9 * (np.einsum("ec,bchw->behw", np.abs(w_exp * P["ib.bn0.g"][:, None]), np.abs(x))
+                       + np.abs(P["ib.bn0.b"])[None, :, None, None])
+    dh = sp_err(x0, h.a) + expit(x0) * dx0
+    ws1 = {"w": np.abs(w_dw * P["ib.bn1.g"][:, None, None])}
+    Dabs = ocnn.depthwise3x3(ocnn.Tape(ws1, record=False), ocnn.Var(np.abs(h.a)), "w").a
+    Ddh = ocnn.depthwise3x3(ocnn.Tape(ws1, record=False), ocnn.Var(dh), "w").a
+    v = ocnn.batchnorm(ocnn.Tape(P, record=False), ocnn.Var(d.a), "ib.bn1", False, running).a
+    dv = Ddh + 10 * u * Dabs + u * (np.abs(P["ib.bn1.b"])[None, :, None, None] + np.abs(v))
+    da = dv + sp_err(v, a.a) + 4 * u * np.abs(a.a)
+    dz = np.einsum("ok,bkhw->bohw", np.abs(w_proj), da)
     s2 = np.abs(P["ib.bn2.g"])[None, :, None, None]
-    prop = np.einsum("ok,bkhw->bohw", np.abs(w_proj), np.abs(a.a) + s1 * Dk)
-    bound = UB * np.abs(y_ref) + UB * s2 * prop
+    # BN2 folded the same way: BF16(scale * w_p) and BF16(shift)
+    dz_fold = 2.0 ** -9 * (np.einsum("ok,bkhw->bohw", np.abs(w_proj * P["ib.bn2.g"][:, None]), np.abs(a.a))
+                           + np.abs(P["ib.bn2.b"])[None, :, None, None])
+    bound = 2 * (s2 * dz + dz_fold + 2.0 ** -9 * np.abs(y_ref) + 1e-6 * np.abs(y_ref).max())
 
     dev = "cuda"
     T = lambda v, dt=torch.float32: torch.tensor(np.ascontiguousarray(v), dtype=dt, device=dev)
@@ -99,13 +128,15 @@ def test_fused_inverted_bottleneck_matches_oracle_per_element(helm, C, B, H, W):
     yg = torch.empty_like(xg)
     ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     L = helm.lib()
-    helm._lib.check(L.helm_ib_bf16(helm._ptr(xg), B, H, W, C, helm._ptr(T(w_exp)), helm._ptr(T(fold["ib.bn0"])),
-                                   helm._ptr(T(w_dw)), helm._ptr(T(fold["ib.bn1"])), helm._ptr(T(w_proj)),
-                                   helm._ptr(T(fold["ib.bn2"])), helm._ptr(yg), helm._ptr(ws), ws.numel(),
-                                   helm._stream()), "helm_ib_bf16")
+    # device copies held in names: a temporary's memory could be reused by the next one
+    args = [T(w_exp), T(fold["ib.bn0"]), T(w_dw), T(fold["ib.bn1"]), T(w_proj), T(fold["ib.bn2"])]
+    helm._lib.check(L.helm_ib_bf16(helm._ptr(xg), B, H, W, C, *[helm._ptr(t) for t in args], helm._ptr(yg),
+                                   helm._ptr(ws), ws.numel(), helm._stream()), "helm_ib_bf16")
     y = np.transpose(yg.double().cpu().numpy(), (0, 3, 1, 2))
     err = np.abs(y - y_ref)
     worst = float((err / bound).max())
+    rel2 = float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+    print(f"IB C={C} {B}x{H}x{W}: worst error/bound {worst:.3f}, 2-norm relative error {rel2:.2e}")
     assert worst <= 1.0, (worst, float(err.max()), float(np.abs(y_ref).max()))
     assert helm.device_errors() == 0
 
@@ -141,17 +172,76 @@ def test_implicit_layer_matches_oracle_per_element(helm, m, B):
     assert worst <= 1.0, worst
 
 
+def _forward_rounded(P, R, r, kf, skip):
+    """The oracle network's evaluation-mode forward composed from the oracle's own layer
+    functions, with every activation the GPU stores rounded to the GPU's storage type at
+    the same place: the encoder input and every conv output (after its fused additions)
+    to BF16, inside the fused bottleneck the expanded activations to FP16 and the
+    depthwise output to BF16 (its weights are FP16), the implicit layer's output to
+    BF16.  Arithmetic between the roundings stays FP64, so what remains between this and
+    the GPU is FP32 accumulation order and the rare rounding flip it causes."""
+    tp = ocnn.Tape(P, record=False)
+    V = ocnn.Var
+    bf = lambda v: V(_bf(v.a))
+
+    def cba(x, cn, bn, stride, add=None, transposed=False):
+        z = ocnn.conv_bn_act(tp, x, cn, bn, stride, False, R, transposed=transposed)
+        return bf(ocnn.add(tp, z, add) if add is not None else z)
+
+    def ib(x, nm):
+        h = V(_f16(ocnn.softplus(tp, ocnn.batchnorm(tp, ocnn.conv1x1(tp, x, nm + ".exp.w"), nm + ".bn0", False,
+                                                      R)).a))
+        a = bf(ocnn.softplus(tp, ocnn.batchnorm(tp, ocnn.depthwise3x3(tp, h, nm + ".dw.w"), nm + ".bn1", False, R)))
+        return bf(ocnn.add(tp, x, ocnn.batchnorm(tp, ocnn.conv1x1(tp, a, nm + ".proj.w"), nm + ".bn2", False, R)))
+
+    B, I, _ = r.shape
+    s = np.sqrt((np.abs(r) ** 2).reshape(B, -1).mean(axis=1))
+    rc = omg.restrict(r) / s[:, None, None]
+    x = V(_bf(np.stack([rc.real, rc.imag], axis=1)))
+    e = V(_bf(kf))
+    encs = []
+    for k in range(3):
+        p = f"e.dm{k + 1}"
+        e = cba(e, p + ".conv0", p + ".bn0", 2)
+        e = cba(e, p + ".conv1", p + ".bn1", 1)
+        e = cba(e, p + ".conv2", p + ".bn2", 1)
+        encs.append(e)
+    feats = []
+    for k in range(3):
+        p = f"s.l{k + 1}"
+        x = cba(x, p + ".conv", p + ".bn", 1 if k == 0 else 2, add=encs[k])
+        x = ib(x, p + ".ib")
+        feats.append(x)
+    x = cba(x, "s.l4.conv0", "s.l4.bn0", 1 if skip else 2)
+    x = cba(x, "s.l4.conv1", "s.l4.bn1", 1)
+    x = cba(x, "s.l4.conv2", "s.l4.bn2", 1)
+    m = ocnn.coarsest_size(I, skip)
+    ghat = ocnn.build_ghat(P, m).astype(np.complex64).astype(np.complex128)
+    x = bf(ocnn.implicit_layer(tp, x, "s.imp.K", ghat))
+    for k in range(3):
+        p = f"s.up{k + 1}"
+        x = cba(x, p + ".convT", p + ".bn0", 1 if (k == 0 and skip) else 2, transposed=True)
+        x = cba(x, p + ".conv1", p + ".bn1", 1)
+        x = cba(x, p + ".conv2", p + ".bn2", 1, add=feats[2 - k])
+    pr = ocnn.conv1x1(tp, x, "s.proj.w", "s.proj.b").a
+    return omg.prolong(pr[:, 0] + 1j * pr[:, 1]) * s[:, None, None]
+
+
 def test_network_forward_at_the_benchmark_shape(helm):
     """I = 576 (512^2 plus the 32-cell layer), skip threshold 256 (coarsest level I/16 =
-    36, the benchmark's plan), batch 8, the committed trained weights: the GPU network
-    against the oracle's forward on samples 0 and 7 (the eval-mode forward treats
-    samples independently).  The GPU rounds some 40 stored activations to BF16; the
-    2-norm error is bounded by 2 % (about sqrt(40) BF16 roundings of relative 2^-9
-    with a gain of 2), every element by 2^-4 |ref| + 2^-4 RMS(ref)."""
+    36, the benchmark's plan), batch 8, the committed trained weights, on samples 0 and
+    7 (the evaluation-mode forward treats samples independently):
+    * against the oracle's forward with the GPU's storage roundings applied at the same
+      places (the GPU's BF16 weights, FP16 depthwise weights, activations rounded as
+      stored): per element |e - ref| <= 2^-7 (|ref| + RMS(ref)), the room FP32
+      accumulation order leaves through occasional one-ulp rounding flips;
+    * against the plain FP64 oracle forward (only the weights rounded): 2-norm within
+      4 %, the accumulated effect of some 40 BF16-stored activations."""
     from paper_2306_17486_gb300 import train as T
+    wpath = os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz")
     net = helm.Cnn(skip_threshold=256)
-    T.load_weights(net, os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz"))
-    d = np.load(os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz"))
+    T.load_weights(net, wpath)
+    d = np.load(wpath)
     I, abl, B = 576, 32, 8
     kap = synth.grf_kappa(512, abl, 8.0, seed=10).astype(np.float32).astype(np.float64)
     oh = 2 * np.pi / 10 / kap.max()
@@ -159,7 +249,6 @@ def test_network_forward_at_the_benchmark_shape(helm):
     net.set_problem(p)
     r = synth.random_complex((B, I, I), 12).astype(np.complex64).astype(np.complex128)
     e = net.apply(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
-    # the oracle with the GPU's BF16 conv weights
     flat = d["params"].astype(np.float64)
     Pd, off = {}, 0
     for name, shape, *_ in ocnn.param_spec(16):
@@ -172,14 +261,20 @@ def test_network_forward_at_the_benchmark_shape(helm):
     for name, c in ocnn.bn_names(16):
         R[name] = (run[off:off + c], run[off + c:off + 2 * c])
         off += 2 * c
+    P16 = dict(Pd)
+    for k in range(3):
+        nm = f"s.l{k + 1}.ib.dw.w"
+        P16[nm] = _f16(Pd[nm])
     on = ocnn.Network(Pd, R, c0=16)
     op = ohz.Problem(kap, abl, omega_h=oh)
     kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
     for i in (0, B - 1):
+        ref_r = _forward_rounded(P16, R, r[i:i + 1], kf, skip=False)[0]
+        rms = np.sqrt(np.mean(np.abs(ref_r) ** 2))
+        worst = float((np.abs(e[i] - ref_r) / (2.0 ** -7 * (np.abs(ref_r) + rms))).max())
+        err_r = np.linalg.norm(e[i] - ref_r) / np.linalg.norm(ref_r)
         ref, _ = on.forward(r[i:i + 1], kf, train=False, skip=False)
-        ref = ref[0]
-        err = np.linalg.norm(e[i] - ref) / np.linalg.norm(ref)
-        assert err < 2e-2, (i, err)
-        rms = np.sqrt(np.mean(np.abs(ref) ** 2))
-        worst = float((np.abs(e[i] - ref) / (2.0 ** -4 * (np.abs(ref) + rms))).max())
-        assert worst <= 1.0, (i, worst, err)
+        err = np.linalg.norm(e[i] - ref[0]) / np.linalg.norm(ref[0])
+        print(f"sample {i}: rounding-aware max ratio {worst:.3f}, 2-norm {err_r:.2e}; plain 2-norm {err:.2e}")
+        assert worst <= 1.0, (i, worst, err_r)
+        assert err < 4e-2, (i, err)
