@@ -8,7 +8,10 @@ relative residual 1e-6 (true FP64 residual).  Inputs are generated once and resi
 in HBM before timing; the Krylov basis (11 x 64 x 576^2 complex64 = 1.9 GB per model)
 is far larger than L2, so no flush is needed between steps.
 
-Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same line carries `workload_1152`: the 1024^2 grid (plus a 64-cell layer, 1152^2
+nodes, 5-level V-cycle), 2 slowness models x 16 point sources, each arm timed once.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--skip-1152]
         (N > 1: launched by torchrun, one replica per GPU, independent models per rank)
 """
 from __future__ import annotations
@@ -161,6 +164,64 @@ def _vcycle_bytes(N: int, levels: int, B: int):
         down += 8 * n + 2 * n
         up += 8 * n + 2 * n + 8 * n
     return {"k_resid_restrict": down, "k_prolong_smooth": up}
+
+
+# The 1024^2 workload: 1024^2 interior + 64-cell absorbing layer = 1152^2 nodes, 5-level
+# V-cycle (coarsest 72^2), two seeded GRF slowness models x 16 point sources, maxit 4000
+# (SL-MG alone needs more than the paper's 2000 here)
+N1K_INT, N1K_ABL, N1K_LEVELS, N1K_MODELS, N1K_RHS, N1K_MAXIT = 1024, 64, 5, 2, 16, 4000
+
+
+def run_1152(helm, net, dev, rank: int):
+    """ms per RHS to 1e-6 on the 1152^2 workload: SL-MG alone, CNN+SL-MG with the network on
+    every CNN_EVERY-th step, and the paper's schedule (every step); one timed pass of all
+    right-hand sides per arm after an untimed warm-up solve, inputs resident in HBM."""
+    import torch
+    import synth
+    probs, bs = [], []
+    for k in range(N1K_MODELS):
+        kap = synth.grf_kappa(N1K_INT, N1K_ABL, 8.0, seed=20 + N1K_MODELS * rank + k)
+        oh = 2.0 * np.pi / (10.0 * float(kap.max()))
+        probs.append(helm.Problem(torch.tensor(kap, dtype=torch.float32, device=dev), N1K_ABL, oh, levels=N1K_LEVELS))
+        bs.append(torch.tensor(synth.random_point_sources(N1K_INT + 2 * N1K_ABL, N1K_ABL, N1K_RHS,
+                                                          seed=2000 + N1K_MODELS * rank + k),
+                               dtype=torch.complex64, device=dev))
+    N = N1K_INT + 2 * N1K_ABL
+    xs = [torch.zeros((N1K_RHS, N, N), dtype=torch.complex128, device=dev) for _ in range(N1K_MODELS)]
+    for p in probs:
+        p.workspace(N1K_RHS, RESTART, net)
+
+    def arm(cnn, every, maxit=N1K_MAXIT):
+        stats = []
+        for k in range(N1K_MODELS):
+            xs[k].zero_()
+            if cnn:
+                net.set_problem(probs[k])
+            _, st = helm.fgmres_solve(probs[k], bs[k], xs[k], cnn=net if cnn else None, restart=RESTART, rtol=RTOL,
+                                      maxit=maxit, warmup_iters=3, cnn_every=every)
+            stats.append(st)
+        return np.concatenate(stats)
+
+    arm(False, 1, 30)
+    arm(True, CNN_EVERY, 30)
+    torch.cuda.synchronize()
+    out = {"workload": "helmholtz-1152sq-2kappa-x16rhs-fgmres10", "grid": N, "interior": N1K_INT, "abl": N1K_ABL,
+           "mg_levels": N1K_LEVELS, "kappa_models": N1K_MODELS, "rhs_per_model": N1K_RHS, "maxit": N1K_MAXIT}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, cnn, every in (("value", True, CNN_EVERY), ("mg_only", False, 1), ("paper_schedule", True, 1)):
+        torch.cuda.synchronize()
+        e0.record()
+        st = arm(cnn, every)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (N1K_MODELS * N1K_RHS)
+        rec = {"ms_per_rhs": round(ms, 3), "iterations_mean": round(float(st["iters"].mean()), 1),
+               "converged_frac": float(np.mean(st["status"] == 1)), "max_true_rel_res": float(st["rel_res_true"].max())}
+        out[name] = rec
+    out["speedup_vs_mg_only"] = round(out["mg_only"]["ms_per_rhs"] / out["value"]["ms_per_rhs"], 3)
+    out["paper_schedule_speedup_vs_mg_only"] = round(out["mg_only"]["ms_per_rhs"] / out["paper_schedule"]["ms_per_rhs"],
+                                                     3)
+    return out
 
 
 def run_gpu(args, rank: int, world: int):
@@ -322,6 +383,8 @@ def run_gpu(args, rank: int, world: int):
                              "iterations_max": int(pp_all["iters"].max()),
                              "converged_frac": float(np.mean(pp_all["status"] == 1)),
                              "max_true_rel_res": float(pp_all["rel_res_true"].max())}
+    if not args.skip_1152:
+        out["workload_1152"] = run_1152(helm, net, dev, rank)
     out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
     out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
     if rank == 0:
@@ -551,6 +614,7 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--weights", default=None)
     ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--skip-1152", action="store_true", help="leave out the 1152^2 (1024^2 interior) workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
