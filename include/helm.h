@@ -108,6 +108,13 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
                         const helm_mg_opts* opts, void* stream, helm_problem** out);
 int helm_problem_destroy(helm_problem* p);
 
+/* Recompute problem p's setup fields in place for a new slowness model kappa_dev (same
+ * grid, absorbing layer, gamma0 and multigrid options) and frequency omega_h; the
+ * problem's device arrays keep their addresses, so work captured against them (a
+ * helm_solver_plan) stays valid.  A network's cached encodings of p become stale:
+ * call helm_cnn_set_problem again.  Synchronises `stream`. */
+int helm_problem_update(helm_problem* p, const float* kappa_dev, double omega_h, void* stream);
+
 /* Grid size of multigrid level `level` (0 = finest). */
 int helm_problem_level_shape(const helm_problem* p, int level, int* nx, int* ny);
 
@@ -214,6 +221,33 @@ void helm_fgmres_opts_default(helm_fgmres_opts* o);
 int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b, void* x, int batch,
                       const helm_fgmres_opts* opts, const int* maxit_dev, helm_fgmres_stats* stats_dev,
                       void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * A captured solver for repeated solves of one batch shape (mixed-size serving: one
+ * plan per grid size).  helm_solver_plan_create binds the problem, the network (NULL:
+ * SL V-cycle only), the right-hand-side buffer b (complex64 [batch][ny][nx]), the
+ * solution buffer x (complex128, the initial guess is zero), the options and the
+ * workspace (helm_workspace_size), runs every kind of restart cycle once, then records
+ * each kind (the network's warm-up cycle and a regular cycle) as a CUDA graph on
+ * `stream`, which must be a non-default stream.  In the captured cycles the network
+ * runs on every right-hand side of the batch and the output of those that fell back to
+ * the V-cycle (helm_fgmres_opts.fallback) is zeroed on the device, so no host decision
+ * is needed inside a cycle; per right-hand side the arithmetic is that of
+ * helm_fgmres_solve.
+ * helm_solver_plan_solve solves for the current contents of b: the restart setup, then
+ * one graph launch per restart cycle with one host read of the active count between
+ * launches; per-RHS statistics as in helm_fgmres_solve.  Between solves the caller may
+ * overwrite b, update the problem in place (helm_problem_update) and recompute the
+ * network's encodings (helm_cnn_set_problem); changing the network's parameters needs a
+ * new plan (HELM_ESTATE), as do encodings computed for another problem.  The buffers
+ * and workspace must stay allocated while the plan lives.
+ */
+typedef struct helm_solver_plan helm_solver_plan;
+int helm_solver_plan_create(const helm_problem* p, const helm_cnn* cnn, const void* b, void* x, int batch,
+                            const helm_fgmres_opts* opts, void* ws, size_t ws_bytes, void* stream,
+                            helm_solver_plan** out);
+int helm_solver_plan_solve(helm_solver_plan* plan, const int* maxit_dev, helm_fgmres_stats* stats_dev, void* stream);
+int helm_solver_plan_destroy(helm_solver_plan* plan);
 
 /*
  * One convolution of the encoder-solver network on the tcgen05 tensor cores

@@ -206,6 +206,63 @@ def fgmres_solve(p: Problem, b: torch.Tensor, x: torch.Tensor | None = None, cnn
     return x, st
 
 
+def problem_update(p: Problem, kappa: torch.Tensor, omega_h: float):
+    """Recompute p's setup in place for a new slowness model of the same grid
+    (helm_problem_update); a network's encodings of p must be recomputed afterwards."""
+    _need(kappa, torch.float32, "kappa")
+    if tuple(kappa.shape) != (p.ny, p.nx) or kappa.device != p.device:
+        raise HelmError(f"kappa must be [{p.ny}, {p.nx}] on {p.device}")
+    check(lib().helm_problem_update(p.handle, _ptr(kappa), omega_h, _stream()), "helm_problem_update")
+    p.omega_h = omega_h
+
+
+class SolverPlan:
+    """A captured FGMRES solver for one problem handle, batch size and options
+    (helm_solver_plan_*): the right-hand sides go into `self.b`, the solution comes out
+    in `self.x`; every restart cycle is one CUDA graph launch on the plan's stream."""
+
+    def __init__(self, p: Problem, batch: int, cnn=None, restart=10, rtol=1e-6, maxit=2000, warmup_iters=3,
+                 reorth=1, cnn_every=1, fallback=True, stream: torch.cuda.Stream | None = None):
+        self.p, self.cnn, self.batch = p, cnn, batch
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=p.device)
+        self.b = torch.zeros((batch, p.ny, p.nx), dtype=torch.complex64, device=p.device)
+        self.x = torch.zeros((batch, p.ny, p.nx), dtype=torch.complex128, device=p.device)
+        self.stats = torch.zeros(batch * STATS_DTYPE.itemsize, dtype=torch.uint8, device=p.device)
+        n = C.c_size_t()
+        check(lib().helm_workspace_size(p.handle, cnn.handle if cnn is not None else None, batch, restart,
+                                        C.byref(n)), "workspace_size")
+        self.ws = torch.empty(n.value, dtype=torch.uint8, device=p.device)
+        self.opts = fgmres_opts(restart, rtol, maxit, warmup_iters, reorth, cnn_every, fallback)
+        h = C.c_void_p()
+        torch.cuda.current_stream(p.device).synchronize()
+        check(lib().helm_solver_plan_create(p.handle, cnn.handle if cnn is not None else None, _ptr(self.b),
+                                            _ptr(self.x), batch, C.byref(self.opts), _ptr(self.ws), self.ws.numel(),
+                                            _stream(self.stream), C.byref(h)), "helm_solver_plan_create")
+        self.handle = h
+
+    def solve(self, maxit_per_rhs: torch.Tensor | None = None):
+        """Solve for the current contents of self.b; returns the per-RHS statistics."""
+        caps = None
+        if maxit_per_rhs is not None:
+            _batch_vec(maxit_per_rhs, self.batch, torch.int32, "maxit_per_rhs", self.b.device)
+            caps = maxit_per_rhs
+        check(lib().helm_solver_plan_solve(self.handle, _ptr(caps), _ptr(self.stats), _stream(self.stream)),
+              "helm_solver_plan_solve")
+        self.stream.synchronize()
+        return np.frombuffer(self.stats.cpu().numpy().tobytes(), dtype=STATS_DTYPE)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().helm_solver_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def device_errors() -> int:
     f = C.c_uint()
     check(lib().helm_device_errors(C.byref(f)), "helm_device_errors")

@@ -52,6 +52,10 @@ PROTOS = {
     "helm_slmg_vcycle_static": (i32, [vp, vp, vp, i32, vp]),
     "helm_fgmres_opts_default": (None, [C.POINTER(FgmresOpts)]),
     "helm_fgmres_solve": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, vp, vp, sz, vp]),
+    "helm_problem_update": (i32, [vp, vp, f64, vp]),
+    "helm_solver_plan_create": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, sz, vp, C.POINTER(vp)]),
+    "helm_solver_plan_solve": (i32, [vp, vp, vp, vp]),
+    "helm_solver_plan_destroy": (i32, [vp]),
     "helm_datagen_pairs": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]),
     "helm_datagen_workspace_size": (i32, [vp, i32, i32, C.POINTER(sz)]),
     "helm_device_errors": (i32, [C.POINTER(C.c_uint)]),

@@ -421,7 +421,7 @@ size_t cnn_forward_bytes(const helm_cnn* c, int I, int B) {
 // e = s Net(r / s), s = RMS(r), in inference mode, scratch from `cv`
 int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float2* e, int B, Carve& cv,
                       cudaStream_t st) {
-  if (c->enc_prob != p || c->enc_version != c->param_version) {
+  if (c->enc_prob != p || c->enc_version != c->param_version || c->enc_pversion != p->version) {
     set_error("cnn: encodings not computed for this problem (call helm_cnn_set_problem)");
     return HELM_ESTATE;
   }
@@ -476,6 +476,7 @@ int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
   if ((rc = launch_kfeat(p->kappa, p->gamma, p->npts(0), static_cast<__nv_bfloat16*>(ptr[c->kf]), st))) return rc;
   if ((rc = run_layers_infer(c, c->enc_plan, ptr, st))) return rc;
   c->enc_prob = p;
+  c->enc_pversion = p->version;
   c->enc_version = c->param_version;
   return HELM_OK;
 }
@@ -498,9 +499,19 @@ __global__ void k_gather_rows(const float2* __restrict__ in, float2* __restrict_
     d4[i] = s4[i];
 }
 
+// e[b] = 0 where zero_rows[b] != 0 (the right-hand sides that fell back to the V-cycle)
+__global__ void k_zero_rows(float2* __restrict__ e, const int* __restrict__ zero_rows, long n) {
+  const int b = blockIdx.y;
+  if (!zero_rows[b]) return;
+  float4* e4 = reinterpret_cast<float4*>(e + b * n);
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n / 2;
+       i += static_cast<long>(gridDim.x) * blockDim.x)
+    e4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn_, const float2* r, float2* z, int batch,
                        Carve& cv, const VcycleScratch& vs, const int* active, cudaStream_t st, const int* sel,
-                       int nsel) {
+                       int nsel, const int* zero_rows) {
   helm_cnn* cnn = const_cast<helm_cnn*>(cnn_);
   const long n = p->npts(0);
   float2* e = cv.take<float2>(static_cast<size_t>(batch) * n);
@@ -513,8 +524,14 @@ int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn_, const float2
   }
   int rc;
   if (sel == nullptr || nsel < 0) {
-    // every RHS goes through the network
+    // every RHS goes through the network; those flagged in zero_rows then use the plain
+    // V-cycle (e = 0, z = V(r))
     if ((rc = cnn_forward_infer(cnn, p, r, e, batch, cv, st))) return rc;
+    if (zero_rows) {
+      const dim3 g(static_cast<unsigned>(std::min<long>(div_up(n / 2, 256), 512)), batch);
+      HELM_LAUNCH("k_zero_rows", st, k_zero_rows<<<g, 256, 0, st>>>(e, zero_rows, n));
+      HELM_CHECK_LAUNCH("k_zero_rows");
+    }
   } else {
     // only the selected RHS: gather, forward on the compact batch, scatter; e = 0 for
     // the others, whose preconditioner is then the plain V-cycle (z = V(r))
@@ -734,7 +751,7 @@ int helm_cnn_precond_apply(const helm_problem* p, helm_cnn* c, const void* r, vo
     return HELM_EWORKSPACE;
   }
   return helm::launch_cnn_precond(p, c, static_cast<const float2*>(r), static_cast<float2*>(z), batch, cv, vs,
-                                  nullptr, static_cast<cudaStream_t>(stream), nullptr, -1);
+                                  nullptr, static_cast<cudaStream_t>(stream), nullptr, -1, nullptr);
 }
 
 }  // extern "C"

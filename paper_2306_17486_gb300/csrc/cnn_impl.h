@@ -83,6 +83,7 @@ struct helm_cnn {
   bool dirty = true;                  // params/running changed since the last derive()
   // encodings cached for one problem
   const helm_problem* enc_prob = nullptr;
+  unsigned long long enc_pversion = 0;  // enc_prob->version the encodings were computed for
   int enc_I = 0;
   unsigned long long enc_version = 0, param_version = 0;
   void* enc_arena = nullptr;

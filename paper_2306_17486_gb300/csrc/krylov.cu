@@ -16,7 +16,7 @@
 #include <cmath>
 #include <vector>
 
-#include "problem.h"
+#include "cnn_impl.h"
 
 #define MAXV (HELM_MAX_RESTART + 1)
 
@@ -489,7 +489,7 @@ namespace helm {
 // library was built without it.
 int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn, const float2* r, float2* z, int batch,
                        Carve& carve, const VcycleScratch& vs, const int* active, cudaStream_t st,
-                       const int* sel_dev = nullptr, int nsel = -1);
+                       const int* sel_dev = nullptr, int nsel = -1, const int* zero_rows = nullptr);
 size_t cnn_workspace_bytes(const helm_problem* p, const helm_cnn* cnn, int batch);
 
 static void carve_solver(Carve& c, const helm_problem* p, int B, int m, Solver* S) {
@@ -544,6 +544,161 @@ size_t solver_bytes(const helm_problem* p, int batch, int restart) {
 
 }  // namespace helm
 
+namespace helm {
+
+// One FGMRES solve's state: the workspace carve, options and the per-RHS device arrays.
+struct SolveCtx {
+  const helm_problem* p = nullptr;
+  const helm_cnn* cnn = nullptr;
+  const float2* b = nullptr;
+  double2* x = nullptr;
+  int B = 0, m = 0;
+  bool use_cnn = false;
+  helm_fgmres_opts o{};
+  Solver S{};
+  VcycleScratch vs;
+  Carve c{nullptr, 0};
+  long n = 0, vstride = 0;
+  dim3 gs;
+};
+
+static int ctx_setup(SolveCtx& x, const helm_problem* p, const helm_cnn* cnn, const float2* b, double2* xs, int B,
+                     const helm_fgmres_opts* opts, void* ws, size_t ws_bytes) {
+  if (opts)
+    x.o = *opts;
+  else
+    helm_fgmres_opts_default(&x.o);
+  const helm_fgmres_opts& o = x.o;
+  if (o.restart < 1 || o.restart > HELM_MAX_RESTART || o.maxit < 0 || !(o.rtol >= 0.0) || o.cnn_every < 1) {
+    set_error("helm_fgmres_solve: restart must be in [1,%d], maxit >= 0, rtol >= 0, cnn_every >= 1", HELM_MAX_RESTART);
+    return HELM_EINVAL;
+  }
+  x.p = p;
+  x.cnn = cnn;
+  x.b = b;
+  x.x = xs;
+  x.B = B;
+  x.m = o.restart;
+  x.c = Carve(ws, ws_bytes);
+  carve_solver(x.c, p, B, o.restart, &x.S);
+  carve_vcycle(x.c, p, B, &x.vs);
+  if (x.c.overflow || !ws) {
+    set_error("helm_fgmres_solve: workspace of %zu bytes too small (need at least %zu)", ws_bytes, x.c.off);
+    return HELM_EWORKSPACE;
+  }
+  x.n = x.S.n;
+  x.vstride = static_cast<long>(B) * x.n;
+  x.use_cnn = cnn != nullptr;
+  x.S.use_cnn = x.use_cnn ? 1 : 0;
+  x.S.allow_fb = o.fallback ? 1 : 0;
+  x.gs = dim3(x.S.nblk, B);
+  return HELM_OK;
+}
+
+// restart: r = b - A x in FP64, per-RHS status, the next cycle's first basis vector
+static int ctx_restart(SolveCtx& x, cudaStream_t st) {
+  Solver& S = x.S;
+  int r2 = launch_residual_fp64(x.p, x.b, x.x, S.V, S.rpart, S.rblk, x.B, S.active, st);
+  if (r2) return r2;
+  HELM_CUDA(cudaMemsetAsync(S.counter, 0, sizeof(int), st));
+  HELM_LAUNCH("k_fin_restart", st, k_fin_restart<<<x.B, 256, 0, st>>>(S, x.o.rtol));
+  HELM_LAUNCH("k_scale", st, k_scale<<<x.gs, KT, 0, st>>>(S.V, x.n, S.inv, S.cyc));
+  HELM_CHECK_LAUNCH("restart");
+  return HELM_OK;
+}
+
+static int ctx_init(SolveCtx& x, const int* maxit_dev, cudaStream_t st) {
+  Solver& S = x.S;
+  HELM_LAUNCH("k_init_caps", st, k_init_caps<<<div_up(x.B, 128), 128, 0, st>>>(S, x.o.maxit, maxit_dev));
+  launch_dots(0, x.gs, st, S.V, x.vstride, x.b, x.n, S.part, S.nblk, nullptr);
+  HELM_LAUNCH("k_fin_bnorm", st, k_fin_bnorm<<<x.B, 256, 0, st>>>(S));
+  HELM_LAUNCH("k_zero_x", st, k_zero_x<<<dim3(64, x.B), 256, 0, st>>>(x.x, x.n, S.bnorm));
+  HELM_CHECK_LAUNCH("fgmres init");
+  return ctx_restart(x, st);
+}
+
+// number of right-hand sides still in a cycle (synchronises the stream; reports device
+// timeouts)
+static int ctx_active(SolveCtx& x, cudaStream_t st, int* nact) {
+  unsigned int derr = 0;
+  HELM_CUDA(cudaMemcpyAsync(nact, x.S.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HELM_CUDA(cudaMemcpyFromSymbolAsync(&derr, g_helm_device_error, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, st));
+  HELM_CUDA(cudaStreamSynchronize(st));
+  if (derr) {
+    set_error("helm_fgmres_solve: device-side wait timed out (flags 0x%x)", derr);
+    return HELM_ETIMEOUT;
+  }
+  return HELM_OK;
+}
+
+// One restart cycle: Arnoldi steps with the preconditioner, the least-squares solution,
+// x += Z y and the restart residual.  `device_only`: no host decision inside the cycle
+// (for graph capture): the network runs on every right-hand side of the batch and the
+// output of those that fell back to the V-cycle is zeroed on the device; otherwise the
+// right-hand sides that use the network are gathered into one dense batch on the host's
+// reading of the fallback flags.
+static int ctx_cycle(SolveCtx& x, bool warm, bool device_only, cudaStream_t st) {
+  Solver& S = x.S;
+  const int m = x.m, B = x.B;
+  const long n = x.n, vstride = x.vstride;
+  const int mlen = warm ? std::min(x.o.warmup_iters, m) : m;
+  int nsel = 0;
+  if (x.use_cnn && !warm && !device_only) {
+    std::vector<int> act(B), fbv(B), sel;
+    HELM_CUDA(cudaMemcpyAsync(act.data(), S.cyc, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaMemcpyAsync(fbv.data(), S.fb, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(cudaStreamSynchronize(st));
+    for (int bb = 0; bb < B; ++bb)
+      if (act[bb] && !fbv[bb]) sel.push_back(bb);
+    nsel = static_cast<int>(sel.size());
+    if (nsel) HELM_CUDA(cudaMemcpyAsync(S.sel, sel.data(), nsel * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  int rc;
+  for (int j = 0; j < mlen; ++j) {
+    float2* vj = S.V + j * vstride;
+    float2* zj = S.Z + j * vstride;
+    float2* w = S.V + (j + 1) * vstride;
+    if (x.use_cnn && !warm && j % x.o.cnn_every == 0) {
+      Carve cc(x.c.base + x.c.off, x.c.cap - x.c.off);
+      rc = device_only ? launch_cnn_precond(x.p, x.cnn, vj, zj, B, cc, x.vs, S.cyc, st, nullptr, -1, S.fb)
+                       : launch_cnn_precond(x.p, x.cnn, vj, zj, B, cc, x.vs, S.cyc, st, S.sel, nsel);
+    } else {
+      rc = launch_vcycle(x.p, vj, zj, B, x.vs, S.cyc, nullptr, st);
+    }
+    if (rc) return rc;
+    if ((rc = launch_apply(x.p, x.p->massA, zj, nullptr, w, B, 0, S.cyc, st))) return rc;
+    launch_dots(j + 1, x.gs, st, S.V, vstride, w, n, S.part, S.nblk, S.cyc);
+    HELM_LAUNCH("k_fin1", st, k_fin1<<<B, 256, 0, st>>>(S, j + 1));
+    launch_update(j + 1, true, x.gs, st, S.V, vstride, w, n, S.hcol, S.part, S.nblk, S.cyc, nullptr);
+    HELM_LAUNCH("k_fin2", st, k_fin2<<<B, 256, 0, st>>>(S, j, x.o.reorth, x.o.rtol));
+    if (x.o.reorth) {
+      launch_update(j + 1, false, x.gs, st, S.V, vstride, w, n, S.ccol, S.part, S.nblk, S.cyc, S.reo);
+      HELM_LAUNCH("k_fin3", st, k_fin3<<<B, 256, 0, st>>>(S, j, x.o.rtol));
+    }
+    HELM_LAUNCH("k_scale", st, k_scale<<<x.gs, KT, 0, st>>>(w, n, S.inv, S.cyc));
+    HELM_CHECK_LAUNCH("arnoldi step");
+  }
+  HELM_LAUNCH("k_backsolve", st, k_backsolve<<<div_up(B, 64), 64, 0, st>>>(S));
+  HELM_LAUNCH("k_xupdate", st, k_xupdate<<<x.gs, KT, 0, st>>>(x.x, S.Z, vstride, n, S.y, m, S.kcyc, S.active));
+  HELM_CHECK_LAUNCH("x update");
+  return ctx_restart(x, st);
+}
+
+static int ctx_finish(SolveCtx& x, helm_fgmres_stats* stats_dev, cudaStream_t st) {
+  HELM_LAUNCH("k_write_stats", st, k_write_stats<<<div_up(x.B, 128), 128, 0, st>>>(x.S, stats_dev));
+  HELM_CHECK_LAUNCH("stats");
+  return HELM_OK;
+}
+
+}  // namespace helm
+
+struct helm_solver_plan {
+  helm::SolveCtx ctx;
+  cudaGraphExec_t gwarm = nullptr;    // the warm-up cycle (V-cycle only), with a network
+  cudaGraphExec_t gcycle = nullptr;   // a regular restart cycle
+  unsigned long long param_version = 0;
+};
+
 extern "C" {
 
 void helm_fgmres_opts_default(helm_fgmres_opts* o) {
@@ -577,109 +732,118 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b_
     set_error("helm_fgmres_solve: invalid argument");
     return HELM_EINVAL;
   }
-  helm_fgmres_opts o;
-  if (opts_)
-    o = *opts_;
-  else
-    helm_fgmres_opts_default(&o);
-  if (o.restart < 1 || o.restart > HELM_MAX_RESTART || o.maxit < 0 || !(o.rtol >= 0.0) || o.cnn_every < 1) {
-    set_error("helm_fgmres_solve: restart must be in [1,%d], maxit >= 0, rtol >= 0, cnn_every >= 1", HELM_MAX_RESTART);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SolveCtx ctx;
+  int rc = ctx_setup(ctx, p, cnn, static_cast<const float2*>(b_), static_cast<double2*>(x_), B, opts_, ws, ws_bytes);
+  if (rc) return rc;
+  if ((rc = ctx_init(ctx, maxit_dev, st))) return rc;
+  for (int cycle = 0;; ++cycle) {
+    int nact = 0;
+    if ((rc = ctx_active(ctx, st, &nact))) return rc;
+    if (nact == 0) break;
+    const bool warm = ctx.use_cnn && cycle == 0 && ctx.o.warmup_iters > 0;
+    if ((rc = ctx_cycle(ctx, warm, false, st))) return rc;
+  }
+  return ctx_finish(ctx, stats_dev, st);
+}
+
+int helm_solver_plan_create(const helm_problem* p, const helm_cnn* cnn, const void* b, void* x, int batch,
+                            const helm_fgmres_opts* opts, void* ws, size_t ws_bytes, void* stream,
+                            helm_solver_plan** out) {
+  using namespace helm;
+  if (!p || !b || !x || batch <= 0 || !out) {
+    set_error("helm_solver_plan_create: invalid argument");
     return HELM_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const float2* b = static_cast<const float2*>(b_);
-  double2* x = static_cast<double2*>(x_);
-  Carve c(ws, ws_bytes);
-  Solver S;
-  carve_solver(c, p, B, o.restart, &S);
-  VcycleScratch vs;
-  carve_vcycle(c, p, B, &vs);
-  if (c.overflow || !ws) {
-    set_error("helm_fgmres_solve: workspace of %zu bytes too small (need at least %zu)", ws_bytes, c.off);
-    return HELM_EWORKSPACE;
+  if (!st) {
+    set_error("helm_solver_plan_create: a non-default stream is needed for graph capture");
+    return HELM_EINVAL;
   }
-  const long n = S.n;
-  const long vstride = static_cast<long>(B) * n;
-  const int m = o.restart;
-  S.use_cnn = cnn != nullptr ? 1 : 0;
-  S.allow_fb = o.fallback ? 1 : 0;
-  dim3 gs(S.nblk, B);
-  int rc;
-
-  HELM_LAUNCH("k_init_caps", st, k_init_caps<<<div_up(B, 128), 128, 0, st>>>(S, o.maxit, maxit_dev));
-  // ||b||
-  launch_dots(0, gs, st, S.V, vstride, b, n, S.part, S.nblk, nullptr);
-  HELM_LAUNCH("k_fin_bnorm", st, k_fin_bnorm<<<B, 256, 0, st>>>(S));
-  HELM_LAUNCH("k_zero_x", st, k_zero_x<<<dim3(64, B), 256, 0, st>>>(x, n, S.bnorm));
-  HELM_CHECK_LAUNCH("fgmres init");
-
-  auto restart_residual = [&]() -> int {
-    int r2 = launch_residual_fp64(p, b, x, S.V, S.rpart, S.rblk, B, S.active, st);
-    if (r2) return r2;
-    HELM_CUDA(cudaMemsetAsync(S.counter, 0, sizeof(int), st));
-    HELM_LAUNCH("k_fin_restart", st, k_fin_restart<<<B, 256, 0, st>>>(S, o.rtol));
-    HELM_LAUNCH("k_scale", st, k_scale<<<gs, KT, 0, st>>>(S.V, n, S.inv, S.cyc));
-    HELM_CHECK_LAUNCH("restart");
-    return HELM_OK;
+  helm_solver_plan* pl = new helm_solver_plan();
+  auto fail = [&](int code) {
+    helm_solver_plan_destroy(pl);
+    return code;
   };
-  if ((rc = restart_residual())) return rc;
+  int rc = ctx_setup(pl->ctx, p, cnn, static_cast<const float2*>(b), static_cast<double2*>(x), batch, opts, ws,
+                     ws_bytes);
+  if (rc) return fail(rc);
+  SolveCtx& c = pl->ctx;
+  if (c.use_cnn) {
+    const helm_cnn* n = cnn;
+    if (n->enc_prob != p || n->enc_pversion != p->version || n->enc_version != n->param_version) {
+      set_error("helm_solver_plan_create: the network's encodings are not for this problem (helm_cnn_set_problem)");
+      return fail(HELM_ESTATE);
+    }
+    pl->param_version = n->param_version;
+  }
+  // one eager pass of every cycle kind first: kernel attributes and the network's derived
+  // state are set up outside the capture
+  if ((rc = ctx_init(c, nullptr, st))) return fail(rc);
+  if (c.use_cnn && c.o.warmup_iters > 0 && (rc = ctx_cycle(c, true, true, st))) return fail(rc);
+  if ((rc = ctx_cycle(c, false, true, st))) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "plan warm-up"));
+  for (int kind = 0; kind < 2; ++kind) {
+    const bool warm = kind == 0;
+    if (warm && !(c.use_cnn && c.o.warmup_iters > 0)) continue;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamBeginCapture"));
+    rc = ctx_cycle(c, warm, true, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return fail(rc);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamEndCapture"));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGraphInstantiate"));
+    (warm ? pl->gwarm : pl->gcycle) = ex;
+  }
+  *out = pl;
+  return HELM_OK;
+}
 
-  const bool use_cnn = cnn != nullptr;
+int helm_solver_plan_solve(helm_solver_plan* pl, const int* maxit_dev, helm_fgmres_stats* stats_dev, void* stream) {
+  using namespace helm;
+  if (!pl || !stats_dev || !pl->gcycle) {
+    set_error("helm_solver_plan_solve: invalid argument");
+    return HELM_EINVAL;
+  }
+  SolveCtx& c = pl->ctx;
+  if (c.use_cnn) {
+    const helm_cnn* n = c.cnn;
+    if (n->param_version != pl->param_version) {
+      set_error("helm_solver_plan_solve: the network's parameters changed after the plan was made");
+      return HELM_ESTATE;
+    }
+    if (n->enc_prob != c.p || n->enc_pversion != c.p->version || n->enc_version != n->param_version) {
+      set_error("helm_solver_plan_solve: the network's encodings are not for this problem (helm_cnn_set_problem)");
+      return HELM_ESTATE;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // every solve starts from x = 0
+  HELM_CUDA(cudaMemsetAsync(c.x, 0, static_cast<size_t>(c.B) * c.n * sizeof(double2), st));
+  int rc = ctx_init(c, maxit_dev, st);
+  if (rc) return rc;
   for (int cycle = 0;; ++cycle) {
     int nact = 0;
-    HELM_CUDA(cudaMemcpyAsync(&nact, S.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HELM_CUDA(cudaStreamSynchronize(st));
-    unsigned int derr = 0;
-    HELM_CUDA(cudaMemcpyFromSymbol(&derr, g_helm_device_error, sizeof(unsigned int)));
-    if (derr) {
-      set_error("helm_fgmres_solve: device-side wait timed out (flags 0x%x)", derr);
-      return HELM_ETIMEOUT;
-    }
+    if ((rc = ctx_active(c, st, &nact))) return rc;
     if (nact == 0) break;
-    const bool warm = use_cnn && cycle == 0 && o.warmup_iters > 0;
-    const int mlen = warm ? std::min(o.warmup_iters, m) : m;
-    // RHS the network runs on during this cycle: active and not fallen back
-    int nsel = 0;
-    if (use_cnn && !warm) {
-      std::vector<int> act(B), fbv(B), sel;
-      HELM_CUDA(cudaMemcpyAsync(act.data(), S.cyc, B * sizeof(int), cudaMemcpyDeviceToHost, st));
-      HELM_CUDA(cudaMemcpyAsync(fbv.data(), S.fb, B * sizeof(int), cudaMemcpyDeviceToHost, st));
-      HELM_CUDA(cudaStreamSynchronize(st));
-      for (int bb = 0; bb < B; ++bb)
-        if (act[bb] && !fbv[bb]) sel.push_back(bb);
-      nsel = static_cast<int>(sel.size());
-      if (nsel) HELM_CUDA(cudaMemcpyAsync(S.sel, sel.data(), nsel * sizeof(int), cudaMemcpyHostToDevice, st));
-    }
-    for (int j = 0; j < mlen; ++j) {
-      float2* vj = S.V + j * vstride;
-      float2* zj = S.Z + j * vstride;
-      float2* w = S.V + (j + 1) * vstride;
-      if (use_cnn && !warm && j % o.cnn_every == 0) {
-        Carve cc(c.base + c.off, c.cap - c.off);
-        rc = launch_cnn_precond(p, cnn, vj, zj, B, cc, vs, S.cyc, st, S.sel, nsel);
-      } else {
-        rc = launch_vcycle(p, vj, zj, B, vs, S.cyc, nullptr, st);
-      }
-      if (rc) return rc;
-      if ((rc = launch_apply(p, p->massA, zj, nullptr, w, B, 0, S.cyc, st))) return rc;
-      launch_dots(j + 1, gs, st, S.V, vstride, w, n, S.part, S.nblk, S.cyc);
-      HELM_LAUNCH("k_fin1", st, k_fin1<<<B, 256, 0, st>>>(S, j + 1));
-      launch_update(j + 1, true, gs, st, S.V, vstride, w, n, S.hcol, S.part, S.nblk, S.cyc, nullptr);
-      HELM_LAUNCH("k_fin2", st, k_fin2<<<B, 256, 0, st>>>(S, j, o.reorth, o.rtol));
-      if (o.reorth) {
-        launch_update(j + 1, false, gs, st, S.V, vstride, w, n, S.ccol, S.part, S.nblk, S.cyc, S.reo);
-        HELM_LAUNCH("k_fin3", st, k_fin3<<<B, 256, 0, st>>>(S, j, o.rtol));
-      }
-      HELM_LAUNCH("k_scale", st, k_scale<<<gs, KT, 0, st>>>(w, n, S.inv, S.cyc));
-      HELM_CHECK_LAUNCH("arnoldi step");
-    }
-    HELM_LAUNCH("k_backsolve", st, k_backsolve<<<div_up(B, 64), 64, 0, st>>>(S));
-    HELM_LAUNCH("k_xupdate", st, k_xupdate<<<gs, KT, 0, st>>>(x, S.Z, vstride, n, S.y, m, S.kcyc, S.active));
-    HELM_CHECK_LAUNCH("x update");
-    if ((rc = restart_residual())) return rc;
+    const bool warm = cycle == 0 && pl->gwarm;
+    HELM_CUDA(cudaGraphLaunch(warm ? pl->gwarm : pl->gcycle, st));
   }
-  HELM_LAUNCH("k_write_stats", st, k_write_stats<<<div_up(B, 128), 128, 0, st>>>(S, stats_dev));
-  HELM_CHECK_LAUNCH("stats");
+  return ctx_finish(c, stats_dev, st);
+}
+
+int helm_solver_plan_destroy(helm_solver_plan* pl) {
+  if (!pl) return HELM_OK;
+  if (pl->gwarm) cudaGraphExecDestroy(pl->gwarm);
+  if (pl->gcycle) cudaGraphExecDestroy(pl->gcycle);
+  delete pl;
   return HELM_OK;
 }
 

@@ -201,6 +201,51 @@ __global__ void k_sl_mass(const double* __restrict__ k2, const double* __restric
 }
 
 // ----------------------------------------------------------------------------------
+namespace helm {
+
+// The setup kernels of Section 3.1-3.2 for the problem's current kappa source and
+// omega h, into the problem's own arrays (in place; the FP64 kappa^2 and gamma pyramids
+// are temporary and freed again).  Synchronises `st`.
+int run_setup(helm_problem* p, const float* kappa_dev, cudaStream_t st) {
+  const helm_mg_opts& o = p->mg;
+  const int nx = p->nx, ny = p->ny, abl = p->abl;
+  const double omega_h = p->omega_h, gamma0 = p->gamma0;
+  const long n0 = p->npts(0);
+  auto fail = [&](int code) { return code; };
+  // FP64 kappa^2 and gamma pyramids, two levels at a time, in the problem's own scratch
+  // (allocated once, so an in-place update allocates nothing)
+  double *k2a = p->setup64[0], *k2b = p->setup64[1], *ga = p->setup64[2], *gb = p->setup64[3];
+  if (kappa_dev != p->kappa) {
+    cudaError_t ce = cudaMemcpyAsync(p->kappa, kappa_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) return fail(cuda_fail(ce, "copy kappa"));
+  }
+  int nb = static_cast<int>(std::min<long>(div_up(n0, 256), 4096));
+  HELM_LAUNCH("k_setup_fine", st, k_setup_fine<<<nb, 256, 0, st>>>(p->kappa, nx, ny, abl, omega_h, gamma0, o.bc, p->gamma, p->massA, p->massA64, k2a, ga));
+  for (int l = 0; l < o.levels; ++l) {
+    double oh = omega_h * static_cast<double>(1 << l);
+    double fix = (o.boundary_fix && l > 0) ? static_cast<double>((1 << l) - 1) : 0.0;
+    long nl = p->npts(l);
+    int nbl = static_cast<int>(std::min<long>(div_up(nl, 256), 4096));
+    HELM_LAUNCH("k_sl_mass", st, k_sl_mass<<<nbl, 256, 0, st>>>(k2a, ga, p->lnx[l], p->lny[l], oh, o.beta, o.sl_includes_gamma, fix,
+                                   o.bc, o.omega_jacobi, p->massSL[l], p->dinvSL[l]));
+    if (l + 1 < o.levels) {
+      long nc = p->npts(l + 1);
+      int nbc = static_cast<int>(std::min<long>(div_up(nc, 256), 4096));
+      HELM_LAUNCH("k_restrict_avg", st, k_restrict_avg<<<nbc, 256, 0, st>>>(k2a, p->lnx[l], p->lny[l], k2b));
+      HELM_LAUNCH("k_restrict_avg", st, k_restrict_avg<<<nbc, 256, 0, st>>>(ga, p->lnx[l], p->lny[l], gb));
+      std::swap(k2a, k2b);
+      std::swap(ga, gb);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(cuda_fail(e, "problem setup kernels"));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "problem setup sync"));
+  return HELM_OK;
+}
+
+}  // namespace helm
+
 extern "C" {
 
 void helm_mg_opts_default(helm_mg_opts* o) {
@@ -289,43 +334,34 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
       return fail(HELM_ENOMEM);
     }
   }
-  // FP64 kappa^2 and gamma pyramids (two levels at a time), freed at the end
-  double* buf[4] = {nullptr, nullptr, nullptr, nullptr};
-  for (double*& b : buf) {
+  for (double*& b : p->setup64) {
     if (cudaMalloc(&b, n0 * 8) != cudaSuccess) {
+      b = nullptr;
       set_error("helm_problem_create: out of device memory for the setup pyramids");
       return fail(HELM_ENOMEM);
     }
-    tmp.push_back(b);
   }
-  double *k2a = buf[0], *k2b = buf[1], *ga = buf[2], *gb = buf[3];
-  cudaError_t ce = cudaMemcpyAsync(p->kappa, kappa_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, st);
-  if (ce != cudaSuccess) return fail(cuda_fail(ce, "copy kappa"));
-  int nb = static_cast<int>(std::min<long>(div_up(n0, 256), 4096));
-  HELM_LAUNCH("k_setup_fine", st, k_setup_fine<<<nb, 256, 0, st>>>(p->kappa, nx, ny, abl, omega_h, gamma0, o.bc, p->gamma, p->massA, p->massA64, k2a, ga));
-  for (int l = 0; l < o.levels; ++l) {
-    double oh = omega_h * static_cast<double>(1 << l);
-    double fix = (o.boundary_fix && l > 0) ? static_cast<double>((1 << l) - 1) : 0.0;
-    long nl = p->npts(l);
-    int nbl = static_cast<int>(std::min<long>(div_up(nl, 256), 4096));
-    HELM_LAUNCH("k_sl_mass", st, k_sl_mass<<<nbl, 256, 0, st>>>(k2a, ga, p->lnx[l], p->lny[l], oh, o.beta, o.sl_includes_gamma, fix,
-                                   o.bc, o.omega_jacobi, p->massSL[l], p->dinvSL[l]));
-    if (l + 1 < o.levels) {
-      long nc = p->npts(l + 1);
-      int nbc = static_cast<int>(std::min<long>(div_up(nc, 256), 4096));
-      HELM_LAUNCH("k_restrict_avg", st, k_restrict_avg<<<nbc, 256, 0, st>>>(k2a, p->lnx[l], p->lny[l], k2b));
-      HELM_LAUNCH("k_restrict_avg", st, k_restrict_avg<<<nbc, 256, 0, st>>>(ga, p->lnx[l], p->lny[l], gb));
-      std::swap(k2a, k2b);
-      std::swap(ga, gb);
-    }
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(cuda_fail(e, "problem setup kernels"));
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return fail(cuda_fail(e, "problem setup sync"));
-  for (void* t : tmp) cudaFree(t);
+  int rc = run_setup(p, kappa_dev, st);
+  if (rc) return fail(rc);
   *out = p;
   return HELM_OK;
+}
+
+int helm_problem_update(helm_problem* p, const float* kappa_dev, double omega_h, void* stream) {
+  using namespace helm;
+  if (!p || !kappa_dev || !(omega_h > 0.0)) {
+    set_error("helm_problem_update: invalid argument");
+    return HELM_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) {
+    set_error("helm_problem_update: the current device is not the problem's device");
+    return HELM_EINVAL;
+  }
+  p->omega_h = omega_h;
+  const int rc = run_setup(p, kappa_dev, static_cast<cudaStream_t>(stream));
+  ++p->version;
+  return rc;
 }
 
 int helm_problem_destroy(helm_problem* p) {
@@ -338,6 +374,7 @@ int helm_problem_destroy(helm_problem* p) {
     cudaFree(p->massSL[l]);
     cudaFree(p->dinvSL[l]);
   }
+  for (double* b : p->setup64) cudaFree(b);
   delete p;
   return HELM_OK;
 }

@@ -21,6 +21,8 @@ struct helm_problem {
   double2* massA64 = nullptr;                // the same in FP64, for the true residual
   float2* massSL[HELM_MAX_LEVELS] = {};      // SL mass per level
   float2* dinvSL[HELM_MAX_LEVELS] = {};      // omega_J / (4 - massSL)
+  unsigned long long version = 0;            // bumped by helm_problem_update
+  double* setup64[4] = {};                   // FP64 kappa^2 / gamma pyramid scratch of the setup
   long npts(int l = 0) const { return static_cast<long>(lnx[l]) * lny[l]; }
 };
 
