@@ -290,6 +290,26 @@ int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const float* w_e
  */
 int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat, void* y, void* stream);
 
+/* Launch-shape tuning table (process-wide, read at launch time; captured solver plans
+ * keep the shapes they were captured with).  A knob's value for a layer of height
+ * `height` run on `batch` images overrides the kernel family's launch heuristic.
+ * Lookup order: (height, batch), (height, any batch: batch 0), (any: height 0 and
+ * batch 0).  Value 0 removes an entry; values are clamped to what the kernel supports.
+ * HELM_EINVAL for an unknown knob or negative arguments.  The autotuner of the Python
+ * package fills it from timings.  Knobs:
+ *   HELM_TUNE_CONV_ROWS  most output rows per convolution segment (a CTA's unit of
+ *                        work; the heuristic takes as many as the shared-memory budget
+ *                        allows, up to 32)
+ *   HELM_TUNE_IB_SH      output rows per work unit of the 16/32-channel inverted
+ *                        bottleneck (a multiple of 4; the heuristic balances the units
+ *                        over the SMs)                                                */
+#define HELM_TUNE_CONV_ROWS 0
+#define HELM_TUNE_IB_SH 1
+#define HELM_TUNE_KNOBS 2
+int helm_tune_set(int knob, int height, int batch, int value);
+int helm_tune_get(int knob, int height, int batch, int* value);
+int helm_tune_clear(void);
+
 /* Number of kernels the library has launched in this process (all devices). */
 unsigned long long helm_launch_count(void);
 

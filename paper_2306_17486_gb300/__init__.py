@@ -263,6 +263,26 @@ class SolverPlan:
             pass
 
 
+TUNE_KNOBS = {"conv_rows": 0, "ib_sh": 1}
+
+
+def tune_set(knob: str, height: int, batch: int, value: int):
+    """Override a launch heuristic for layers of height `height` run on `batch` images
+    (batch 0: any batch; height 0 with batch 0: every layer); value 0 removes the entry."""
+    check(lib().helm_tune_set(TUNE_KNOBS[knob], int(height), int(batch), int(value)), "helm_tune_set")
+
+
+def tune_get(knob: str, height: int, batch: int) -> int:
+    """The value a launch of that height and batch takes (0: the heuristic)."""
+    v = C.c_int()
+    check(lib().helm_tune_get(TUNE_KNOBS[knob], int(height), int(batch), C.byref(v)), "helm_tune_get")
+    return v.value
+
+
+def tune_clear():
+    check(lib().helm_tune_clear(), "helm_tune_clear")
+
+
 def device_errors() -> int:
     f = C.c_uint()
     check(lib().helm_device_errors(C.byref(f)), "helm_device_errors")

@@ -53,6 +53,9 @@ PROTOS = {
     "helm_fgmres_opts_default": (None, [C.POINTER(FgmresOpts)]),
     "helm_fgmres_solve": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, vp, vp, sz, vp]),
     "helm_problem_update": (i32, [vp, vp, f64, vp]),
+    "helm_tune_set": (i32, [i32, i32, i32, i32]),
+    "helm_tune_get": (i32, [i32, i32, i32, C.POINTER(i32)]),
+    "helm_tune_clear": (i32, []),
     "helm_solver_plan_create": (i32, [vp, vp, vp, vp, i32, C.POINTER(FgmresOpts), vp, sz, vp, C.POINTER(vp)]),
     "helm_solver_plan_solve": (i32, [vp, vp, vp, vp]),
     "helm_solver_plan_destroy": (i32, [vp]),

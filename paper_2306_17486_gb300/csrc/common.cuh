@@ -190,6 +190,10 @@ int make_c64_map(CUtensorMap* out, const void* base, int nx, int ny, int nb, int
 // fill outside the tensor.  A box lands in shared memory as box_h x box_w pixels of 16 B.
 int make_bf16_nhwc_map(CUtensorMap* out, const void* base, int C, int W, int H, int B, int box_w, int box_h);
 
+// Tuned launch-shape value of `knob` for a layer of height `height` on `batch` images
+// (0: none; tune.cu).
+int tune_get(int knob, int height, int batch);
+
 inline int div_up(long a, long b) { return static_cast<int>((a + b - 1) / b); }
 
 // Multiprocessor count of the current device (cached per device).

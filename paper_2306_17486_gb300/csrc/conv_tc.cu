@@ -392,14 +392,33 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     int Lr = 128 * nt + (TAPS == 1 ? 0 : (a.mode == HELM_CONV_S2 || PH == 4 ? a.Po + 2 : 2 * a.Po + 2));
     return Lr | 1;
   };
+  int nsm = 0;
+  int rc = helm::sm_count(&nsm);
+  if (rc) return rc;
   if (TAPS == 1) {
     int tiles = static_cast<int>((budget - std::min(budget, fixed)) / (plane_row * 128));
     tiles = std::max(1, std::min(tiles, 16));
     a.seg_q = 128 * tiles;
   } else {
+    // Rows per segment: a tuned value, the most rows that fit below it; otherwise, among
+    // the row counts whose window fits the budget, the one with the least work on the
+    // busiest SM, counted in MMA steps plus one step of window load and epilogue per
+    // segment (ties: more rows).  Large batches take the most rows that fit; small
+    // ones split images until every SM has work.
+    const int tuned = helm::tune_get(HELM_TUNE_CONV_ROWS, a.Ho, a.B);
+    const int rmax = std::min(a.Ho, tuned > 0 ? tuned : 32);
     int R = 1;
-    for (int r = 2; r <= std::min(a.Ho, 32); ++r)
-      if (fixed + plane_row * window_rows(r * a.Po) <= budget) R = r;
+    long best = -1;
+    for (int r = 1; r <= rmax; ++r) {
+      if (r > 1 && fixed + plane_row * window_rows(r * a.Po) > budget) break;
+      const long segs = static_cast<long>(a.B) * helm::div_up(a.Ho, r);
+      const long steps = helm::div_up(static_cast<long>(r) * a.Po, 128 * Cfg::MT);
+      const long cost = helm::div_up(segs, nsm) * (steps + 1);
+      if (tuned > 0 || best < 0 || cost <= best) {
+        best = cost;
+        R = r;
+      }
+    }
     a.seg_q = R * a.Po;
   }
   a.L = window_rows(a.seg_q);
@@ -411,9 +430,7 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     return HELM_ESHAPE;
   }
   static std::atomic<unsigned long long> attr_done{0};
-  int rc = helm::smem_attr_once(k_conv_tc<CS, COUT, TAPS, PH, MTR>, 227 * 1024, &attr_done);
-  int nsm = 0;
-  if (!rc) rc = helm::sm_count(&nsm);
+  rc = helm::smem_attr_once(k_conv_tc<CS, COUT, TAPS, PH, MTR>, 227 * 1024, &attr_done);
   if (rc) return rc;
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA), TMEM
   // columns (512 per SM) and registers (at most two 288-thread CTAs below 113 registers)

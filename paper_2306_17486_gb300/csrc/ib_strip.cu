@@ -520,7 +520,8 @@ int launch_strip(const helm::IbLaunch& l, cudaStream_t st) {
   int rc = helm::sm_count(&nsm);
   if (rc) return rc;
   a.nsx = helm::div_up(l.W, SW);
-  a.SH = choose_sh(l.B, l.H, a.nsx, nsm);
+  const int tuned = helm::tune_get(HELM_TUNE_IB_SH, l.H, l.B);
+  a.SH = tuned > 0 ? std::min(std::max(4, (tuned / 4) * 4), ((l.H + 3) / 4) * 4) : choose_sh(l.B, l.H, a.nsx, nsm);
   a.nsy = helm::div_up(l.H, a.SH);
   const long units = static_cast<long>(l.B) * a.nsx * a.nsy;
   if (units > (1L << 30)) {

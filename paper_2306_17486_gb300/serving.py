@@ -31,7 +31,7 @@ import time
 import numpy as np
 import torch
 
-from . import Cnn, Problem, SolverPlan, problem_update
+from . import Cnn, Problem, SolverPlan, autotune, problem_update
 from . import train as T
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -126,6 +126,7 @@ def run(sizes=(256, 512, 1024), per_size=4, batch=8, mg_only=False, cnn_every=3,
     """Serve the interleaved request stream; returns the report dict."""
     reqs = make_requests(sizes, per_size, batch, seed)
     first = {r["n"]: r["kappa"] for r in reversed(reqs)}
+    autotune.apply(grids={(bucket_config(n)[0], batch) for n in sizes})   # before the plans are captured
     buckets = {n: Bucket(n, batch, not mg_only, cnn_every, first[n]) for n in sizes}
     if warm:   # one untimed request per bucket
         for n, bk in buckets.items():

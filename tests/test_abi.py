@@ -59,3 +59,22 @@ def test_library_is_in_tree_and_built_for_sm103a(L):
     assert os.path.dirname(_lib.LIB_PATH).startswith(os.path.dirname(os.path.abspath(_lib.__file__)))
     from paper_2306_17486_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_tuning_table_lookup_order(L):
+    v = ctypes.c_int()
+    assert L.helm_tune_clear() == 0
+    assert L.helm_tune_get(0, 576, 64, ctypes.byref(v)) == 0 and v.value == 0       # heuristic
+    assert L.helm_tune_set(0, 0, 0, 16) == 0                                           # any layer
+    assert L.helm_tune_set(0, 576, 0, 8) == 0                                          # height 576, any batch
+    assert L.helm_tune_set(0, 576, 64, 4) == 0                                         # height 576, batch 64
+    for (h, b), want in {(576, 64): 4, (576, 8): 8, (288, 64): 16}.items():
+        assert L.helm_tune_get(0, h, b, ctypes.byref(v)) == 0 and v.value == want, (h, b, v.value)
+    assert L.helm_tune_get(1, 576, 64, ctypes.byref(v)) == 0 and v.value == 0         # other knob untouched
+    assert L.helm_tune_set(0, 576, 64, 0) == 0                                         # removed: next entry
+    assert L.helm_tune_get(0, 576, 64, ctypes.byref(v)) == 0 and v.value == 8
+    assert L.helm_tune_set(2, 576, 64, 4) == -1                                        # no such knob
+    assert L.helm_tune_set(0, 0, 64, 4) == -1                                          # batch without height
+    assert L.helm_tune_set(0, -1, 0, 4) == -1
+    assert L.helm_tune_clear() == 0
+    assert L.helm_tune_get(0, 576, 8, ctypes.byref(v)) == 0 and v.value == 0
