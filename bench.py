@@ -9,9 +9,13 @@ in HBM before timing; the Krylov basis (11 x 64 x 576^2 complex64 = 1.9 GB per m
 is far larger than L2, so no flush is needed between steps.
 
 The same line carries `workload_1152`: the 1024^2 grid (plus a 64-cell layer, 1152^2
-nodes, 5-level V-cycle), 2 slowness models x 16 point sources, each arm timed once.
+nodes, 5-level V-cycle), 2 slowness models x 16 point sources, each arm timed once; and
+`serving`: p50/p99 latency of a burst of mixed-size requests (288^2, 576^2, 1152^2
+nodes, 8 right-hand sides each) served by captured solver plans, with and without the
+network.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--skip-1152]
+        [--skip-serving]
         (N > 1: launched by torchrun, one replica per GPU, independent models per rank)
 """
 from __future__ import annotations
@@ -385,6 +389,8 @@ def run_gpu(args, rank: int, world: int):
                              "max_true_rel_res": float(pp_all["rel_res_true"].max())}
     if not args.skip_1152:
         out["workload_1152"] = run_1152(helm, net, dev, rank)
+    if not args.skip_serving:
+        out["serving"] = run_serving()
     out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
     out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
     if rank == 0:
@@ -394,6 +400,27 @@ def run_gpu(args, rank: int, world: int):
 
 
 WEIGHTS = os.path.join(ROOT, "paper_2306_17486_gb300", "weights", "cnn_grf_multiscale.npz")
+
+# Mixed-size serving: requests for 256^2, 512^2 and 1024^2 interiors (288^2, 576^2,
+# 1152^2 nodes) interleaved, each its own layered+GRF model with 8 point sources,
+# served by captured solver plans, one bucket per size on its own stream and thread
+SERVE_SIZES, SERVE_REQUESTS, SERVE_BATCH = (256, 512, 1024), 3, 8
+
+
+def run_serving():
+    """p50 / p99 request latency and throughput of the serving path, with the network
+    (on every CNN_EVERY-th step) and with SL-MG alone, on the same request stream."""
+    from paper_2306_17486_gb300 import serving
+    out = {"grids": [serving.bucket_config(n)[0] for n in SERVE_SIZES], "requests": SERVE_REQUESTS * len(SERVE_SIZES),
+           "rhs_per_request": SERVE_BATCH, "arrival": "one burst, round robin over the sizes"}
+    for key, mg_only in (("cnn_mg", False), ("mg_only", True)):
+        rep = serving.run(SERVE_SIZES, SERVE_REQUESTS, SERVE_BATCH, mg_only=mg_only, cnn_every=CNN_EVERY)
+        out[key] = {k: rep[k] for k in ("p50_ms", "p99_ms", "makespan_s", "throughput_rhs_per_s")}
+        out[key]["iterations_mean"] = {g: v["iterations_mean"] for g, v in rep["per_grid"].items()}
+        out[key]["converged_frac"] = min(v["converged_frac"] for v in rep["per_grid"].values())
+        if rep["errors"]:
+            out[key]["errors"] = rep["errors"][:3]
+    return out
 
 
 def _network(helm, dev, args):
@@ -615,6 +642,7 @@ def main():
     ap.add_argument("--weights", default=None)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--skip-1152", action="store_true", help="leave out the 1152^2 (1024^2 interior) workload")
+    ap.add_argument("--skip-serving", action="store_true", help="leave out the mixed-size serving run")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

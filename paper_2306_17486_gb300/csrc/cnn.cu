@@ -545,7 +545,7 @@ int launch_cnn_precond(const helm_problem* p, const helm_cnn* cnn_, const float2
     }
   }
   if ((rc = launch_apply(p, p->massA, e, r, rp, batch, 0, active, st))) return rc;   // r' = r - A e
-  return launch_vcycle(p, rp, z, batch, vs, active, nullptr, st, e);                // z = e + V(r')
+  return launch_vcycle(p, rp, z, batch, vs, active, st, e);                // z = e + V(r')
 }
 
 }  // namespace helm

@@ -663,7 +663,7 @@ static int ctx_cycle(SolveCtx& x, bool warm, bool device_only, cudaStream_t st) 
       rc = device_only ? launch_cnn_precond(x.p, x.cnn, vj, zj, B, cc, x.vs, S.cyc, st, nullptr, -1, S.fb)
                        : launch_cnn_precond(x.p, x.cnn, vj, zj, B, cc, x.vs, S.cyc, st, S.sel, nsel);
     } else {
-      rc = launch_vcycle(x.p, vj, zj, B, x.vs, S.cyc, nullptr, st);
+      rc = launch_vcycle(x.p, vj, zj, B, x.vs, S.cyc, st);
     }
     if (rc) return rc;
     if ((rc = launch_apply(x.p, x.p->massA, zj, nullptr, w, B, 0, S.cyc, st))) return rc;

@@ -55,11 +55,10 @@ struct VcycleScratch {
 void carve_vcycle(Carve& c, const helm_problem* p, int batch, VcycleScratch* s);
 
 // Launch one V-cycle (all kernels on `stream`).  `active` (nullable, device int[batch])
-// masks right-hand sides that are skipped.  `rscale` (nullable, device float[batch])
-// multiplies the input r on the fly.
-// `zadd` (nullable) is added to the finest-level output (z = zadd + V(r)).
+// masks right-hand sides that are skipped.  `zadd` (nullable) is added to the
+// finest-level output (z = zadd + V(r)).
 int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, const VcycleScratch& s,
-                  const int* active, const float* rscale, cudaStream_t stream, const float2* zadd = nullptr);
+                  const int* active, cudaStream_t stream, const float2* zadd = nullptr);
 
 // y = c - h^2 A x (c nullable: y = h^2 A x) with the fine Helmholtz mass, masked.
 int launch_apply(const helm_problem* p, const float2* mass, const float2* x, const float2* c, float2* y,

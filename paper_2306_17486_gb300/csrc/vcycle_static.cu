@@ -73,6 +73,6 @@ extern "C" int helm_slmg_vcycle_static(const helm_problem* p, const void* r, voi
   if (rc) return rc;
   helm::Carve c(base, kScratchBytes);
   helm::carve_vcycle(c, p, batch, &s);
-  return helm::launch_vcycle(p, static_cast<const float2*>(r), static_cast<float2*>(z), batch, s, nullptr, nullptr,
+  return helm::launch_vcycle(p, static_cast<const float2*>(r), static_cast<float2*>(z), batch, s, nullptr,
                              static_cast<cudaStream_t>(stream));
 }
