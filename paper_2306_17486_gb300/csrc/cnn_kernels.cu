@@ -243,11 +243,7 @@ __global__ void __launch_bounds__(256) k_dw3x3_row(const bf16* __restrict__ x, i
 
 // ---- implicit layer (Eq. 14), one CTA per (sample, complex channel) -----------------
 // x: channels k (Re) and k + C/2 (Im) of an m x m map; zero-pad to 2m x 2m, DFT,
-// multiply by G_hat_k, inverse DFT, keep the top-left m x m block.  The DFTs are
-// evaluated as dense sums with a twiddle table, skipping the zero half of the
-// padded input and the discarded half of the output.
-// Optionally (gh_out != null) also writes conj(X_hat) . F(pad(gy)) / (2m)^2 for the
-// kernel gradient (backward; then x is the forward input and gy the output gradient).
+// multiply by G_hat_k, inverse DFT, keep the top-left m x m block.
 template <typename TIn>
 __device__ __forceinline__ float2 load_pair(const TIn* p, long idx, int C, int k) {
   return make_float2(static_cast<float>(p[idx * C + k]), static_cast<float>(p[idx * C + k + C / 2]));
@@ -257,121 +253,209 @@ __device__ __forceinline__ float2 load_pair<bf16>(const bf16* p, long idx, int C
   return make_float2(__bfloat162float(p[idx * C + k]), __bfloat162float(p[idx * C + k + C / 2]));
 }
 
-// forward DFT of the zero-padded m x m block in `X` (m x m) into `F` (2m x 2m), using
-// scratch `R` (m x 2m); twiddle W[e] = exp(-2 pi i e / 2m).  The twiddle index u c mod 2m
-// is advanced incrementally (e += u, wrapped) instead of being recomputed per term.
-__device__ __forceinline__ int twiddle_step(int e, int d, int n) {
-  e += d;
-  return e >= n ? e - n : e;
+// The 2m x 2m transforms of the implicit layer run as mixed-radix FFTs (Stockham
+// autosort: every stage reads one buffer and writes the other in natural order, so no
+// digit reversal is needed), batched over the lines of a phase and spread over the
+// CTA's threads:
+//   rows     R[r][.]  = FFT(pad(X[r][.]))                     r < m
+//   columns  R[.][u]  = IFFT(G_hat[.][u] . FFT(pad(R[.][u])))  kept for rows < m
+//   rows     Y[r][c]  = IFFT(R[r][.])[c] / (2m)^2             r, c < m
+// Each phase runs in chunks of cw lines, so that shared memory holds R (m x 2m) and two
+// cw x 2m line buffers.
+// n = 2m is factored into radices 4, 2, 3, 5 and any other prime up to FFT_PMAX (direct
+// DFT of that size); twiddles come from one table W[e] = exp(-2 pi i e / n).
+constexpr int FFT_MAXF = 16;
+constexpr int FFT_PMAX = 16;
+struct FftPlan {
+  int nf;              // stages
+  int f[FFT_MAXF];     // radix of each stage
+};
+
+__device__ __forceinline__ float2 tw(const float2* Wt, int e, bool inv) {
+  const float2 w = Wt[e];
+  return inv ? make_float2(w.x, -w.y) : w;
+}
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ float2 rot_i(float2 v, bool inv) {
+  return inv ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
 }
 
-// The 2m x 2m DFT of the zero-padded input, the product with G_hat and the inverse DFT
-// cropped to the top-left m x m block, with the column stages done in chunks of `cw`
-// columns so that only a 2m x cw block of the spectrum is held at a time:
-//   rows    R[r][u] = sum_c X[r][c] W^(u c)                (r < m: the zero half skipped)
-//   chunk   F[v][u] = G_hat[v][u] sum_r R[r][u] W^(v r),    u in the chunk
-//           R[r][u] = sum_v F[v][u] W^(-v r)                (r < m: the discarded half skipped)
-//   rows    Y[r][c] = (1 / (2m)^2) sum_u R[r][u] W^(-u c)  (c < m)
-// The twiddle index of each term is advanced incrementally.
+// One Stockham stage of radix p over L lines of length n: butterfly j of a line reads
+// x[j + r n/p] (r < p), multiplies input r by W_n^(k r n/(Ns p)) with k = j mod Ns, takes
+// the length-p DFT and writes output r to y[(j / Ns) Ns p + k + r Ns].
+__device__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst, int L, int n, int p, int Ns,
+                          const float2* __restrict__ Wt, bool inv) {
+  const int q = n / p;                 // butterflies per line
+  const int tws = n / (Ns * p);        // twiddle index step per unit of k r
+  const int total = L * q;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int line = t / q, j = t - line * q;
+    const float2* s = src + static_cast<long>(line) * n + j;
+    const int k = j % Ns;
+    float2* d = dst + static_cast<long>(line) * n + (j / Ns) * Ns * p + k;
+    const int ek = k * tws;            // twiddle index of input 1; input r takes r ek (< n)
+    if (p == 4) {
+      float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv)), v2 = cmul(s[2 * q], tw(Wt, 2 * ek, inv)),
+             v3 = cmul(s[3 * q], tw(Wt, 3 * ek, inv));
+      const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), b0 = cadd(v1, v3), b1 = rot_i(csub(v1, v3), inv);
+      d[0] = cadd(a0, b0);
+      d[Ns] = cadd(a1, b1);
+      d[2 * Ns] = csub(a0, b0);
+      d[3 * Ns] = csub(a1, b1);
+    } else if (p == 2) {
+      const float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv));
+      d[0] = cadd(v0, v1);
+      d[Ns] = csub(v0, v1);
+    } else if (p == 3) {
+      const float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv)), v2 = cmul(s[2 * q], tw(Wt, 2 * ek, inv));
+      const float2 t1 = cadd(v1, v2);
+      const float2 t2 = make_float2(v0.x - 0.5f * t1.x, v0.y - 0.5f * t1.y);
+      // sqrt(3)/2 (v1 - v2) turned by -i (forward) or +i (inverse)
+      const float2 t3 = rot_i(cscale(csub(v1, v2), 0.86602540378443865f), inv);
+      d[0] = cadd(v0, t1);
+      d[Ns] = cadd(t2, t3);
+      d[2 * Ns] = csub(t2, t3);
+    } else {
+      // any other radix: direct DFT of length p with W_p^(a b) = W_n^((a b mod p) q)
+      float2 v[FFT_PMAX];
+      for (int r = 0; r < p; ++r) v[r] = r ? cmul(s[r * q], tw(Wt, r * ek, inv)) : s[0];
+      for (int a = 0; a < p; ++a) {
+        float2 acc = v[0];
+        for (int r = 1; r < p; ++r) acc = cadd(acc, cmul(v[r], tw(Wt, ((a * r) % p) * q, inv)));
+        d[a * Ns] = acc;
+      }
+    }
+  }
+}
+
+// All stages over L lines, ping-ponging between a and b; returns the buffer holding the
+// result.  Callers synchronise the CTA before the first stage.
+__device__ float2* fft_lines(float2* a, float2* b, int L, int n, const FftPlan& plan, const float2* Wt, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < plan.nf; ++s) {
+    fft_stage(a, b, L, n, plan.f[s], Ns, Wt, inv);
+    __syncthreads();
+    Ns *= plan.f[s];
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// Eq. 14 for one (sample b, complex channel k): y = crop(IFFT(G_hat_k . FFT(pad(x)))),
+// or with conj_g the adjoint (conj(G_hat_k)); accumulate adds into y (FP32 output only).
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat,
-                                                  int conj_g, TOut* __restrict__ y, int accumulate, int cw) {
+                                                  int conj_g, TOut* __restrict__ y, int accumulate, int cw,
+                                                  FftPlan plan) {
   const int b = blockIdx.y, k = blockIdx.x;
   const int n = 2 * m;
   extern __shared__ float2 ism[];
-  float2* Wt = ism;               // n: W^e = exp(-2 pi i e / n)
-  float2* X = Wt + n;             // m*m   (input, later output)
-  float2* R = X + m * m;          // m*n
-  float2* F = R + m * n;          // n*cw  (one column chunk of the spectrum)
+  float2* Wt = ism;               // n
+  float2* R = Wt + n;             // m x n: the rows' spectra, later the columns' results
+  float2* P0 = R + m * n;         // cw x n ping-pong buffers of the line transforms
+  float2* P1 = P0 + cw * n;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     float s, c;
     sincospif(-2.f * e / n, &s, &c);
     Wt[e] = make_float2(c, s);
   }
   const long base = static_cast<long>(b) * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) X[i] = load_pair<TIn>(x, base + i, C, k);
-  __syncthreads();
-  for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
-    const int r = i / n, u = i % n;
-    float2 acc = make_float2(0.f, 0.f);
-    int e = 0;
-    for (int c = 0; c < m; ++c) {
-      acc = cadd(acc, cmul(X[r * m + c], Wt[e]));
-      e = twiddle_step(e, u, n);
+  for (int r0 = 0; r0 < m; r0 += cw) {
+    const int w = min(cw, m - r0);
+    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
+      const int r = i / n, c = i - r * n;
+      P0[i] = c < m ? load_pair<TIn>(x, base + (r0 + r) * m + c, C, k) : make_float2(0.f, 0.f);
     }
-    R[i] = acc;
+    __syncthreads();
+    const float2* rs = fft_lines(P0, P1, w, n, plan, Wt, false);
+    for (int i = threadIdx.x; i < w * n; i += blockDim.x) R[r0 * n + i] = rs[i];
+    __syncthreads();
   }
-  __syncthreads();
   const float2* G = ghat + static_cast<long>(k) * n * n;
   for (int u0 = 0; u0 < n; u0 += cw) {
     const int w = min(cw, n - u0);
-    for (int i = threadIdx.x; i < n * w; i += blockDim.x) {
-      const int v = i / w, uu = i % w;
-      float2 acc = make_float2(0.f, 0.f);
-      int e = 0;
-      for (int r = 0; r < m; ++r) {
-        acc = cadd(acc, cmul(R[r * n + u0 + uu], Wt[e]));
-        e = twiddle_step(e, v, n);
-      }
-      float2 g = G[v * n + u0 + uu];
-      if (conj_g) g.y = -g.y;
-      F[v * cw + uu] = cmul(acc, g);
+    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
+      const int l = i / n, v = i - l * n;
+      P0[i] = v < m ? R[v * n + u0 + l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m * w; i += blockDim.x) {
-      const int r = i / w, uu = i % w;
-      float2 acc = make_float2(0.f, 0.f);
-      int e = 0;
-      for (int v = 0; v < n; ++v) {
-        const float2 t = Wt[e];
-        acc = cadd(acc, cmul(F[v * cw + uu], make_float2(t.x, -t.y)));
-        e = twiddle_step(e, r, n);
-      }
-      R[r * n + u0 + uu] = acc;   // this chunk's columns of R are no longer needed forward
+    float2* fs = fft_lines(P0, P1, w, n, plan, Wt, false);
+    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
+      const int l = i / n, v = i - l * n;
+      float2 g = G[static_cast<long>(v) * n + u0 + l];
+      if (conj_g) g.y = -g.y;
+      fs[i] = cmul(fs[i], g);
+    }
+    __syncthreads();
+    const float2* is = fft_lines(fs, fs == P0 ? P1 : P0, w, n, plan, Wt, true);
+    for (int i = threadIdx.x; i < w * m; i += blockDim.x) {
+      const int l = i / m, v = i - l * m;
+      R[v * n + u0 + l] = is[l * n + v];
     }
     __syncthreads();
   }
   const float sc = 1.f / static_cast<float>(n * n);
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const int r = i / m, c = i % m;
-    float2 acc = make_float2(0.f, 0.f);
-    int e = 0;
-    for (int u = 0; u < n; ++u) {
-      const float2 t = Wt[e];
-      acc = cadd(acc, cmul(R[r * n + u], make_float2(t.x, -t.y)));
-      e = twiddle_step(e, c, n);
-    }
-    X[i] = cscale(acc, sc);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const long idx = (base + i) * C;
-    if constexpr (sizeof(TOut) == 2) {
-      y[idx + k] = __float2bfloat16_rn(X[i].x);
-      y[idx + k + C / 2] = __float2bfloat16_rn(X[i].y);
-    } else {
-      if (accumulate) {
-        y[idx + k] += X[i].x;
-        y[idx + k + C / 2] += X[i].y;
+  for (int r0 = 0; r0 < m; r0 += cw) {
+    const int w = min(cw, m - r0);
+    // the chunk's rows of R are consumed here, so they serve as one of the two buffers
+    const float2* ys = fft_lines(R + r0 * n, P0, w, n, plan, Wt, true);
+    for (int i = threadIdx.x; i < w * m; i += blockDim.x) {
+      const int r = i / m, c = i - r * m;
+      const float2 v = cscale(ys[r * n + c], sc);
+      const long idx = (base + (r0 + r) * m + c) * C;
+      if constexpr (sizeof(TOut) == 2) {
+        y[idx + k] = __float2bfloat16_rn(v.x);
+        y[idx + k + C / 2] = __float2bfloat16_rn(v.y);
       } else {
-        y[idx + k] = X[i].x;
-        y[idx + k + C / 2] = X[i].y;
+        if (accumulate) {
+          y[idx + k] += v.x;
+          y[idx + k + C / 2] += v.y;
+        } else {
+          y[idx + k] = v.x;
+          y[idx + k + C / 2] = v.y;
+        }
       }
     }
+    __syncthreads();
   }
+}
+
+// Radices of n (4s first, then 2, 3, 5, other primes); false if a prime factor exceeds
+// FFT_PMAX or there are too many stages.
+static bool fft_plan(int n, FftPlan* p) {
+  p->nf = 0;
+  const int pref[] = {4, 2, 3, 5};
+  for (int r : pref)
+    while (n % r == 0) {
+      if (p->nf == FFT_MAXF) return false;
+      p->f[p->nf++] = r;
+      n /= r;
+    }
+  for (int r = 7; n > 1; r += 2)
+    while (n % r == 0) {
+      if (r > FFT_PMAX || p->nf == FFT_MAXF) return false;
+      p->f[p->nf++] = r;
+      n /= r;
+    }
+  return true;
 }
 
 // shared memory of k_implicit with column chunks of width cw
 static size_t implicit_chunk_smem(int m, int cw) {
-  return static_cast<size_t>(2 * m + m * m + m * 2 * m + 2 * m * cw) * sizeof(float2);
+  const size_t n = 2 * m;
+  return (n + m * n + 2 * static_cast<size_t>(cw) * n) * sizeof(float2);
 }
-// the widest chunk (in equal parts of the 2m columns) that fits 200 KB, or 0
+// the widest chunk (in equal parts of the 2m columns) whose CTA fits 76 KB (three CTAs
+// per SM), else 200 KB; 0 if none does
 static int implicit_chunk(int m) {
   const int n = 2 * m;
-  for (int parts = 1; parts <= n; ++parts) {
-    const int cw = (n + parts - 1) / parts;
-    if (implicit_chunk_smem(m, cw) <= 200 * 1024) return cw;
-  }
+  for (size_t cap : {size_t(76) * 1024, size_t(200) * 1024})
+    for (int parts = 1; parts <= n; ++parts) {
+      const int cw = (n + parts - 1) / parts;
+      if (implicit_chunk_smem(m, cw) <= cap) return cw;
+    }
   return 0;
 }
 
@@ -576,32 +660,42 @@ int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const f
 
 size_t implicit_smem(int m) { return static_cast<size_t>(2 * m + m * m + m * 2 * m + 4 * m * m) * sizeof(float2); }
 
-int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat, bf16* y, cudaStream_t st) {
-  const int cw = implicit_chunk(m);
-  if (!cw) {
+// chunk width and FFT plan of an m x m implicit layer, or an error
+static int implicit_setup(int m, int* cw, FftPlan* plan) {
+  *cw = implicit_chunk(m);
+  if (!*cw) {
     set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
     return HELM_ESHAPE;
   }
+  if (!fft_plan(2 * m, plan)) {
+    set_error("implicit layer: 2m = %d has a prime factor above %d", 2 * m, FFT_PMAX);
+    return HELM_ESHAPE;
+  }
+  return HELM_OK;
+}
+
+int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat, bf16* y, cudaStream_t st) {
+  int cw;
+  FftPlan plan;
+  if (int rc = implicit_setup(m, &cw, &plan)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<bf16, bf16>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit", st,
               k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(x, m, C, ghat, 0, y, 0,
-                                                                                             cw));
+                                                                                             cw, plan));
   HELM_CHECK_LAUNCH("k_implicit");
   return HELM_OK;
 }
 
 int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* ghat, float* gx, cudaStream_t st) {
-  const int cw = implicit_chunk(m);
-  if (!cw) {
-    set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
-    return HELM_ESHAPE;
-  }
+  int cw;
+  FftPlan plan;
+  if (int rc = implicit_setup(m, &cw, &plan)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<float, float>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit_adj", st,
               k_implicit<float, float><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(gy, m, C, ghat, 1, gx, 1,
-                                                                                               cw));
+                                                                                               cw, plan));
   HELM_CHECK_LAUNCH("k_implicit_adj");
   return HELM_OK;
 }
