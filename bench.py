@@ -132,11 +132,15 @@ def _peaks():
 
 
 # DRAM bytes per RHS of one application of a kernel family (all its launches), measured
-# by ncu (dram__bytes.sum.per_second x duration) on captures at the bench shape (64 RHS x
-# 576^2, tensors larger than the 129 MB L2): the matvec (one launch, 298.3 MB) and the
-# three fused inverted bottlenecks (297.7 + 125.9 + 43.4 MB).  Kernels captured only on
-# small cases (their tensors stay in L2) or changed since their capture are absent.
-NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64, "k_ib_fused": 467.03e6 / 64}
+# by ncu (dram__bytes.sum.per_second x duration) on a capture at the bench shape (64 RHS
+# x 576^2, tensors larger than the 129 MB L2): the matvec (one launch, 298.3 MB).
+# Kernels captured only on small cases (their tensors stay in L2) or changed since their
+# capture are absent.
+NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64}
+
+# FP32 lane peak for kernels bound by plain arithmetic: 152 SMs x 128 FP32 lanes x 2 FLOP
+# (fused multiply-add) x 2.07 GHz
+FP32_LANE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _net_layer_bytes(I: int, B: int):
@@ -145,7 +149,8 @@ def _net_layer_bytes(I: int, B: int):
     written once, BF16 NHWC.  Returns {kernel family: bytes}."""
     h = I // 2
     px = lambda n: n * n * B
-    ib = sum(4 * c * px(h >> k) for k, c in enumerate((16, 32, 64)))           # read x, write y
+    ib_strip = 4 * 16 * px(h) + 4 * 32 * px(h // 2)                            # read x, write y
+    ib_fused = 4 * 64 * px(h // 4)
     conv = 0
     conv += (2 * 2 + 2 * 16) * px(h)                                             # l1: 2 -> 16
     conv += 2 * 16 * px(h) + 2 * 32 * px(h // 2)                                 # l2: s2 16 -> 32
@@ -154,9 +159,18 @@ def _net_layer_bytes(I: int, B: int):
     for c_in, c_out, n in ((64, 64, h // 4), (64, 32, h // 2), (32, 16, h)):     # up modules
         conv += 2 * c_in * px(n // 2) + 2 * c_out * px(n)                        # transposed s2
         conv += 10 * c_out * px(n)                                               # conv1, conv2 (+ skip read)
-    implicit = 2 * (2 * 64) * px(I // 16)
     proj = 2 * 16 * px(h) + 8 * px(I)
-    return {"k_ib_fused": ib, "k_conv_tc": conv, "k_implicit": implicit, "k_proj_prolong": proj}
+    return {"k_ib_strip": ib_strip, "k_ib_fused": ib_fused, "k_conv_tc": conv, "k_proj_prolong": proj}
+
+
+def _implicit_flops(I: int, B: int, C: int = 64):
+    """Algorithmic FLOPs of one implicit layer (Eq. 14) as FFTs: per (sample, complex
+    channel) 6m transforms of length n = 2m (m row and 2m column forward/inverse, m row
+    inverse) at the conventional 5 n log2 n real FLOPs each, plus the product with G_hat
+    (6 FLOPs per spectral point)."""
+    m = I // 16
+    n = 2 * m
+    return B * (C // 2) * (6 * m * 5 * n * np.log2(n) + 6 * n * n)
 
 
 def _vcycle_bytes(N: int, levels: int, B: int):
@@ -373,7 +387,7 @@ def run_gpu(args, rank: int, world: int):
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(kappas[0], bs[0][:1].cpu().numpy(), float(iters.mean()))
     # compact per-kernel figures, then the comparison the metric is about, last
-    out["roofline_kernels"] = [{k: r[k] for k in ("kernel", "achieved", "frac", "launch_ms", "share_of_step")}
+    out["roofline_kernels"] = [{k: r[k] for k in ("kernel", "bound", "achieved", "frac", "launch_ms", "share_of_step")}
                                for r in roofs if r is not roof]
     out["kernel_shares"] = [[n, c, round(t, 1), round(t / tot_ms, 3)] for n, c, t in prof[:6]]
     out["iterations"] = {"mean": round(float(iters.mean()), 1), "max": int(iters.max()), "converged_frac": conv,
@@ -505,6 +519,15 @@ def _rooflines(helm, L, C, net, P, dev, hbm, src, step_prof):
                     "launch_ms": round(t_launch * 1e3, 4),
                     "traffic": round(tr * N_RHS / per_call) if tr is not None else None,
                     "share_of_step": round(share.get(name, 0.0) / tot, 4) if tot else None})
+    if "k_implicit" in prof:
+        cnt, ms = prof["k_implicit"]
+        t_launch = ms / cnt * 1e-3
+        fl = _implicit_flops(N, N_RHS) / (cnt / reps)
+        ach = fl / t_launch / 1e12
+        out.append({"kernel": "k_implicit", "bound": "alu", "achieved": round(ach, 2), "peak": round(FP32_LANE_TFLOPS, 1),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_LANE_TFLOPS, 4), "peak_source": "derived",
+                    "flops_per_launch": round(fl), "launch_ms": round(t_launch * 1e3, 4), "traffic": None,
+                    "share_of_step": round(share.get("k_implicit", 0.0) / tot, 4) if tot else None})
     out.sort(key=lambda d: -(d["share_of_step"] or 0.0))
     return out
 

@@ -42,7 +42,7 @@ namespace {
 
 // ---- the two V-cycle legs -------------------------------------------------------------
 // Both legs stream the fine grid in strips 64 values wide (two per lane of a warp).  A
-// CTA takes a work unit = one strip for 8 right-hand sides: one TMA load brings the
+// CTA takes a work unit = one strip for 4 right-hand sides: one TMA load brings the
 // strip of dinv (one array per level, shared by all right-hand sides) and one per active
 // right-hand side brings its strip of r (and, for the prolongation, of the coarse
 // correction), all zero-filled outside the grid (the Dirichlet padding).  Two warps
@@ -53,17 +53,18 @@ namespace {
 // completely, which leaves them without branches.  CTAs are persistent, take units in
 // a strided order and keep the next unit's loads in flight while they process the
 // current one (two buffers).
-constexpr int VL_RHS = 8;                       // right-hand sides per unit
+constexpr int VL_RHS = 4;                       // right-hand sides per unit
+constexpr int VL_CTAS = 2;                      // CTAs per SM (shared memory)
 constexpr int VL_WARPS = 2 * VL_RHS;            // two bands per right-hand side
 constexpr int VL_THREADS = 32 * VL_WARPS;
 constexpr int VS_W = 64;                        // strip width (fine values)
 constexpr int RC_TW = 30;                       // restriction: coarse columns per strip
-constexpr int RC_TH = 10;                       //   coarse rows per strip
+constexpr int RC_TH = 8;                        //   coarse rows per strip
 constexpr int RS_H = 2 * RC_TH + 3;             //   strip rows: fine rows 2 J0 - 2 .. 2 J1 + 2
 constexpr int RC_HB = RC_TH / 2;                //   coarse rows per band
 constexpr int RB_H = 2 * RC_HB + 3;             //   strip rows a band walks
 constexpr int PS_TW = 60;                       // prolongation: output columns per strip
-constexpr int PS_TH = 16;                       //   output rows per strip
+constexpr int PS_TH = 12;                       //   output rows per strip
 constexpr int PS_H = PS_TH + 2;                 //   strip rows: one halo row above and below
 constexpr int PS_HB = PS_TH / 2;                //   output rows per band
 constexpr int PB_H = PS_HB + 2;                 //   strip rows a band walks
@@ -76,7 +77,9 @@ constexpr int RS_BUF = (1 + VL_RHS) * RS_TILE;                     // dinv + r s
 constexpr int PS_BUF = (1 + VL_RHS) * PS_TILE + VL_RHS * PE_TILE;  // dinv + r + ec strips
 constexpr size_t RS_SMEM = 2 * RS_BUF * sizeof(float2) + 128;   // + alignment slack
 constexpr size_t PS_SMEM = 2 * PS_BUF * sizeof(float2) + 128;
-static_assert(RS_SMEM <= 227 * 1024 && PS_SMEM <= 227 * 1024, "two buffers per CTA");
+static_assert(VL_CTAS * (RS_SMEM + 1024) <= 228 * 1024 && VL_CTAS * (PS_SMEM + 1024) <= 228 * 1024,
+              "two buffers per CTA, VL_CTAS CTAs per SM");
+static_assert(PS_HB % 2 == 0, "a band starts on an odd fine row");
 static_assert((RS_TILE * sizeof(float2)) % 128 == 0 && (PS_TILE * sizeof(float2)) % 128 == 0,
               "strips start on 128-byte boundaries");
 
@@ -146,7 +149,7 @@ __device__ __forceinline__ void cta_units(uint64_t* bars, long units, long per_g
 // Residual and full-weighting restriction (Eq. 6 with the h^2 scaling of the coarse
 // operator): u = dinv r (the pre-sweep from zero), q = r - S u = (1 - omega) r + the sum
 // of the neighbours' u, rc = 4 I_h^H q with the [1 2 1] x [1 2 1] / 16 stencil.
-// Unit: (group of 8 right-hand sides, band of RC_TH coarse rows, strip of RC_TW coarse
+// Unit: (group of VL_RHS right-hand sides, band of RC_TH coarse rows, strip of RC_TW coarse
 // columns); lane l of a warp holds fine columns 2 l, 2 l + 1 of the strip and produces
 // coarse column l - 1 (lanes 1 .. 30).
 __global__ void __launch_bounds__(VL_THREADS) k_resid_restrict(const __grid_constant__ CUtensorMap mr,
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(VL_THREADS) k_resid_restrict(const __grid_cons
 
 // Prolongation, correction and post-sweep (Eq. 8 and the damped Jacobi post-sweep):
 // u2 = dinv r + I_H^h ec (the pre-sweep recomputed from r), z = (1 - omega) u2 +
-// dinv (r + the sum of the neighbours' u2), plus zadd when given.  Unit: (group of 8
+// dinv (r + the sum of the neighbours' u2), plus zadd when given.  Unit: (group of VL_RHS
 // right-hand sides, band of PS_TH rows, strip of PS_TW columns starting at x0); lane l
 // holds columns xa = x0 - 2 + 2 l and xa + 1 and writes them for lanes 1 .. 30.  The
 // bilinear prolongation of the pair needs ec at coarse columns xa / 2 and xa / 2 + 1,
@@ -954,7 +957,7 @@ int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, 
     if ((rc = make_c64_map(&md, p->dinvSL[l], p->lnx[l], p->lny[l], 1, VS_W, RS_H))) return rc;
     const long units = static_cast<long>(div_up(batch, VL_RHS)) * div_up(p->lnx[l + 1], RC_TW) *
                        div_up(p->lny[l + 1], RC_TH);
-    const int grid = static_cast<int>(std::min<long>(units, nsm));
+    const int grid = static_cast<int>(std::min<long>(units, static_cast<long>(VL_CTAS) * nsm));
     HELM_LAUNCH("k_resid_restrict", st,
                 k_resid_restrict<<<grid, VL_THREADS, RS_SMEM, st>>>(m, md, s.rc[l + 1], p->lnx[l], p->lny[l], batch,
                                                                     active, onemw));
@@ -984,7 +987,7 @@ int launch_vcycle(const helm_problem* p, const float2* r, float2* z, int batch, 
     if ((rc = make_c64_map(&me, s.ec[l + 1], p->lnx[l + 1], p->lny[l + 1], batch, PE_W, PE_H))) return rc;
     if ((rc = make_c64_map(&md, p->dinvSL[l], p->lnx[l], p->lny[l], 1, VS_W, PS_H))) return rc;
     const long units = static_cast<long>(div_up(batch, VL_RHS)) * div_up(p->lnx[l], PS_TW) * div_up(p->lny[l], PS_TH);
-    const int grid = static_cast<int>(std::min<long>(units, nsm));
+    const int grid = static_cast<int>(std::min<long>(units, static_cast<long>(VL_CTAS) * nsm));
     HELM_LAUNCH("k_prolong_smooth", st,
                 k_prolong_smooth<<<grid, VL_THREADS, PS_SMEM, st>>>(mr, me, md, zout, p->lnx[l], p->lny[l], batch,
                                                                     active, l == 0 ? zadd : nullptr, onemw));
