@@ -132,11 +132,13 @@ def _peaks():
 
 
 # DRAM bytes per RHS of one application of a kernel family (all its launches), measured
-# by ncu (dram__bytes.sum.per_second x duration) on a capture at the bench shape (64 RHS
-# x 576^2, tensors larger than the 129 MB L2): the matvec (one launch, 298.3 MB).
-# Kernels captured only on small cases (their tensors stay in L2) or changed since their
-# capture are absent.
-NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64}
+# by ncu on captures at the bench shape (64 RHS x 576^2, tensors larger than the 129 MB
+# L2): the matvec (one launch), the V-cycle legs (three launches each) and the network's
+# families (dram__bytes_read.sum + dram__bytes_write.sum over one application).  A kernel
+# changed since its capture is removed from this table.
+NCU_TRAFFIC_PER_RHS = {"k_apply": 298.29e6 / 64, "k_resid_restrict": 252.9e6 / 64, "k_prolong_smooth": 417.2e6 / 64,
+                       "k_conv_tc": 2033.9e6 / 64, "k_ib_strip": 414.2e6 / 64, "k_ib_fused": 42.7e6 / 64,
+                       "k_proj_prolong": 296.2e6 / 64}
 
 # FP32 lane peak for kernels bound by plain arithmetic: 152 SMs x 128 FP32 lanes x 2 FLOP
 # (fused multiply-add) x 2.07 GHz
