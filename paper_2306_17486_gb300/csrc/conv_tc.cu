@@ -91,7 +91,7 @@ constexpr int CONV_EPI_WARPS = 8;
 constexpr int CONV_THREADS = 32 * (CONV_EPI_WARPS + 1);
 
 template <int CS, int COUT, int TAPS, int PH, int MTR>
-__global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_conv_tc(const ConvArgs a) {
   using Cfg = ConvCfg<CS, COUT, TAPS, PH, MTR>;
   constexpr int G = Cfg::G;
   constexpr int MT = Cfg::MT;
@@ -275,20 +275,48 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
     } else {
       // ---- epilogues: TMEM lane (tid mod 128) <-> virtual pixel of M-tile mt ----
       const int mt = MT == 2 ? chalf : 0;
+      const int cfirst = MT == 2 ? 0 : 16 * chalf, cstep = MT == 2 ? 16 : 32;
+      // the residual inputs of one 16-channel chunk (two 16-byte vectors each), loaded
+      // before the accumulator is read so that their latency overlaps the TMEM load
+      // (and, for a step's first chunk, the wait for the MMAs)
+      auto load_adds = [&](bool ok_px, long pix, long pix2, int c0, uint4 (&r1)[2], uint4 (&r2)[2]) {
+        if (ok_px && a.y && a.add1) {
+          const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
+          r1[0] = pp[0];
+          r1[1] = pp[1];
+        }
+        if (ok_px && a.y && a.add2) {
+          const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
+          r2[0] = pp[0];
+          r2[1] = pp[1];
+        }
+      };
       for (int j = 0; j < nsteps; ++j) {
         const uint32_t g = gstep + j, buf = g % Cfg::NBUF, use = g / Cfg::NBUF;
-        ok = mbar_wait_bounded(&full[buf], use & 1u, HELM_DEVERR_MMA_WAIT) && ok;
-        tc::fence_after_sync();
         const int q = qs + 128 * (MT * j + mt) + (tid & 127);
         const int y = q / a.Po, x = q - y * a.Po;
-        const bool valid = ok && q < qe && x < a.Wo;
+        const bool inside = q < qe && x < a.Wo;
+        auto pixel = [&](int ph, long& pix, long& pix2) {
+          const int oy = PH == 4 ? 2 * y + (ph >> 1) : y, ox = PH == 4 ? 2 * x + (ph & 1) : x;
+          pix = (static_cast<long>(b) * a.Hout + oy) * a.Wout + ox;
+          pix2 = (static_cast<long>(b / a.add2_div) * a.Hout + oy) * a.Wout + ox;
+        };
+        uint4 n1[2], n2[2];
+        {
+          long pix, pix2;
+          pixel(0, pix, pix2);
+          load_adds(inside, pix, pix2, cfirst, n1, n2);
+        }
+        ok = mbar_wait_bounded(&full[buf], use & 1u, HELM_DEVERR_MMA_WAIT) && ok;
+        tc::fence_after_sync();
+        const bool valid = ok && inside;
 #pragma unroll 1
         for (int ph = 0; ph < PH; ++ph) {
-          const int oy = PH == 4 ? 2 * y + (ph >> 1) : y, ox = PH == 4 ? 2 * x + (ph & 1) : x;
-          const long pix = (static_cast<long>(b) * a.Hout + oy) * a.Wout + ox;
-          const long pix2 = (static_cast<long>(b / a.add2_div) * a.Hout + oy) * a.Wout + ox;
+          long pix, pix2;
+          pixel(ph, pix, pix2);
 #pragma unroll 1
-          for (int c0 = MT == 2 ? 0 : 16 * chalf; c0 < COUT; c0 += (MT == 2 ? 16 : 32)) {
+          for (int c0 = cfirst; c0 < COUT; c0 += cstep) {
+            if (ph > 0 || c0 != cfirst) load_adds(inside, pix, pix2, c0, n1, n2);   // the first came before the wait
             float v[16];
             tc::ld16(tmem + (static_cast<uint32_t>(lane_q * 32) << 16) + buf * Cfg::STEP + mt * Cfg::ACC + ph * COUT +
                          c0,
@@ -306,21 +334,17 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv_tc(const ConvArgs a) {
                 v[i] = a.act ? tc::softplus_fast(t) : t;
               }
               if (a.add1) {
-                const uint4* pp = reinterpret_cast<const uint4*>(a.add1 + pix * COUT + c0);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                  uint4 u = pp[h];
-                  const bf16* e = reinterpret_cast<const bf16*>(&u);
+                  const bf16* e = reinterpret_cast<const bf16*>(&n1[h]);
 #pragma unroll
                   for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
                 }
               }
               if (a.add2) {
-                const uint4* pp = reinterpret_cast<const uint4*>(a.add2 + pix2 * COUT + c0);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                  uint4 u = pp[h];
-                  const bf16* e = reinterpret_cast<const bf16*>(&u);
+                  const bf16* e = reinterpret_cast<const bf16*>(&n2[h]);
 #pragma unroll
                   for (int i = 0; i < 8; ++i) v[8 * h + i] += __bfloat162float(e[i]);
                 }
