@@ -139,11 +139,14 @@ def test_fgmres_matches_oracle_solution(helm):
         true = np.linalg.norm(b[i] - op.A(xs[i])) / np.linalg.norm(b[i])
         assert true <= 1e-6 and abs(true - st["rel_res_true"][i]) <= 1e-9
         xr, res = ofg.fgmres(op.A, b[i], np.zeros_like(b[i]), mg, 10, 1e-12, 4000)
-        # error bound from the residual: ||e|| <= ||A^-1|| ||r||; measured against the
-        # oracle's own iteration count at 1e-6
-        _, res6 = ofg.fgmres(op.A, b[i], np.zeros_like(b[i]), mg, 10, 1e-6, 4000)
+        # the residual bounds the error only through ||A^-1||, so the GPU's error at a 1e-6
+        # residual is compared with the FP64 oracle's own error at the same residual
+        xr6, res6 = ofg.fgmres(op.A, b[i], np.zeros_like(b[i]), mg, 10, 1e-6, 4000)
         rel_err = np.linalg.norm(xs[i] - xr) / np.linalg.norm(xr)
+        oracle_err = np.linalg.norm(xr6 - xr) / np.linalg.norm(xr)
+        print(f"rhs {i}: solution error GPU {rel_err:.2e}, FP64 oracle at the same tolerance {oracle_err:.2e}")
         assert rel_err < 1e-3, rel_err
+        assert rel_err <= 10 * oracle_err + 1e-6, (rel_err, oracle_err)
         assert abs(st["iters"][i] - res6.iters) <= max(3, 0.1 * res6.iters), (st["iters"][i], res6.iters)
 
 
