@@ -262,8 +262,9 @@ __device__ __forceinline__ float2 load_pair<bf16>(const bf16* p, long idx, int C
 //   rows     Y[r][c]  = IFFT(R[r][.])[c] / (2m)^2             r, c < m
 // Each phase runs in chunks of cw lines, so that shared memory holds R (m x 2m) and two
 // cw x 2m line buffers.
-// n = 2m is factored into radices 4, 2, 3, 5 and any other prime up to FFT_PMAX (direct
-// DFT of that size); twiddles come from one table W[e] = exp(-2 pi i e / n).
+// n = 2m is factored into radices 8, 9, 4, 2, 3, 5 (8 and 9 as in-register 4 x 2 and
+// 3 x 3 decompositions) and any other prime up to FFT_PMAX (direct DFT of that size);
+// twiddles come from one table W[e] = exp(-2 pi i e / n).
 constexpr int FFT_MAXF = 16;
 constexpr int FFT_PMAX = 16;
 struct FftPlan {
@@ -278,6 +279,24 @@ __device__ __forceinline__ float2 tw(const float2* Wt, int e, bool inv) {
 // multiply by -i (forward) or +i (inverse)
 __device__ __forceinline__ float2 rot_i(float2 v, bool inv) {
   return inv ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+// length-4 DFT in place (forward: W4 = -i)
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3, bool inv) {
+  const float2 a0 = cadd(x0, x2), a1 = csub(x0, x2), b0 = cadd(x1, x3), b1 = rot_i(csub(x1, x3), inv);
+  x0 = cadd(a0, b0);
+  x1 = cadd(a1, b1);
+  x2 = csub(a0, b0);
+  x3 = csub(a1, b1);
+}
+// length-3 DFT in place (forward: W3 = exp(-2 pi i / 3))
+__device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2, bool inv) {
+  const float2 t1 = cadd(x1, x2);
+  const float2 t2 = make_float2(x0.x - 0.5f * t1.x, x0.y - 0.5f * t1.y);
+  // sqrt(3)/2 (x1 - x2) turned by -i (forward) or +i (inverse)
+  const float2 t3 = rot_i(cscale(csub(x1, x2), 0.86602540378443865f), inv);
+  x0 = cadd(x0, t1);
+  x1 = cadd(t2, t3);
+  x2 = csub(t2, t3);
 }
 
 // One Stockham stage of radix p over L lines of length n: butterfly j of a line reads
@@ -294,27 +313,64 @@ __device__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ d
     const int k = j % Ns;
     float2* d = dst + static_cast<long>(line) * n + (j / Ns) * Ns * p + k;
     const int ek = k * tws;            // twiddle index of input 1; input r takes r ek (< n)
-    if (p == 4) {
+    if (p == 8) {
+      // two length-4 DFTs of the even and odd inputs, then W8^k on the odd half
+      float2 v[8];
+      v[0] = s[0];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v[r] = cmul(s[r * q], tw(Wt, r * ek, inv));
+      dft4(v[0], v[2], v[4], v[6], inv);
+      dft4(v[1], v[3], v[5], v[7], inv);
+      const float h = 0.70710678118654752f;
+      const float2 o1 = cscale(cadd(v[3], rot_i(v[3], inv)), h);       // W8^1 = (1 -+ i)/sqrt(2)
+      const float2 o2 = rot_i(v[5], inv);                               // W8^2 = -+ i
+      const float2 o3 = cscale(csub(rot_i(v[7], inv), v[7]), h);       // W8^3 = (-1 -+ i)/sqrt(2)
+      d[0] = cadd(v[0], v[1]);
+      d[4 * Ns] = csub(v[0], v[1]);
+      d[Ns] = cadd(v[2], o1);
+      d[5 * Ns] = csub(v[2], o1);
+      d[2 * Ns] = cadd(v[4], o2);
+      d[6 * Ns] = csub(v[4], o2);
+      d[3 * Ns] = cadd(v[6], o3);
+      d[7 * Ns] = csub(v[6], o3);
+    } else if (p == 9) {
+      // 3 x 3: length-3 DFTs over n1 for each n2, twiddles W9^(n2 k1), length-3 DFTs over n2
+      float2 v[9];
+      v[0] = s[0];
+#pragma unroll
+      for (int r = 1; r < 9; ++r) v[r] = cmul(s[r * q], tw(Wt, r * ek, inv));
+#pragma unroll
+      for (int n2 = 0; n2 < 3; ++n2) dft3(v[n2], v[3 + n2], v[6 + n2], inv);
+      const int e9 = n / 9;
+      v[4] = cmul(v[4], tw(Wt, e9, inv));        // n2 = 1, k1 = 1
+      v[7] = cmul(v[7], tw(Wt, 2 * e9, inv));    // n2 = 1, k1 = 2
+      v[5] = cmul(v[5], tw(Wt, 2 * e9, inv));    // n2 = 2, k1 = 1
+      v[8] = cmul(v[8], tw(Wt, 4 * e9, inv));    // n2 = 2, k1 = 2
+#pragma unroll
+      for (int k1 = 0; k1 < 3; ++k1) {
+        dft3(v[3 * k1], v[3 * k1 + 1], v[3 * k1 + 2], inv);
+        d[k1 * Ns] = v[3 * k1];
+        d[(k1 + 3) * Ns] = v[3 * k1 + 1];
+        d[(k1 + 6) * Ns] = v[3 * k1 + 2];
+      }
+    } else if (p == 4) {
       float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv)), v2 = cmul(s[2 * q], tw(Wt, 2 * ek, inv)),
              v3 = cmul(s[3 * q], tw(Wt, 3 * ek, inv));
-      const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), b0 = cadd(v1, v3), b1 = rot_i(csub(v1, v3), inv);
-      d[0] = cadd(a0, b0);
-      d[Ns] = cadd(a1, b1);
-      d[2 * Ns] = csub(a0, b0);
-      d[3 * Ns] = csub(a1, b1);
+      dft4(v0, v1, v2, v3, inv);
+      d[0] = v0;
+      d[Ns] = v1;
+      d[2 * Ns] = v2;
+      d[3 * Ns] = v3;
     } else if (p == 2) {
       const float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv));
       d[0] = cadd(v0, v1);
       d[Ns] = csub(v0, v1);
     } else if (p == 3) {
-      const float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv)), v2 = cmul(s[2 * q], tw(Wt, 2 * ek, inv));
-      const float2 t1 = cadd(v1, v2);
-      const float2 t2 = make_float2(v0.x - 0.5f * t1.x, v0.y - 0.5f * t1.y);
-      // sqrt(3)/2 (v1 - v2) turned by -i (forward) or +i (inverse)
-      const float2 t3 = rot_i(cscale(csub(v1, v2), 0.86602540378443865f), inv);
-      d[0] = cadd(v0, t1);
-      d[Ns] = cadd(t2, t3);
-      d[2 * Ns] = csub(t2, t3);
+      float2 v0 = s[0], v1 = cmul(s[q], tw(Wt, ek, inv)), v2 = cmul(s[2 * q], tw(Wt, 2 * ek, inv));
+      dft3(v0, v1, v2, inv);
+      d[0] = v0;
+      d[Ns] = v1;
+      d[2 * Ns] = v2;
     } else {
       // any other radix: direct DFT of length p with W_p^(a b) = W_n^((a b mod p) q)
       float2 v[FFT_PMAX];
@@ -345,8 +401,9 @@ __device__ float2* fft_lines(float2* a, float2* b, int L, int n, const FftPlan& 
 
 // Eq. 14 for one (sample b, complex channel k): y = crop(IFFT(G_hat_k . FFT(pad(x)))),
 // or with conj_g the adjoint (conj(G_hat_k)); accumulate adds into y (FP32 output only).
+// Registers are capped so that three CTAs share an SM at m = 36 (62.8 KB each).
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat,
+__global__ void __launch_bounds__(256, 3) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat,
                                                   int conj_g, TOut* __restrict__ y, int accumulate, int cw,
                                                   FftPlan plan) {
   const int b = blockIdx.y, k = blockIdx.x;
@@ -422,11 +479,11 @@ __global__ void __launch_bounds__(256) k_implicit(const TIn* __restrict__ x, int
   }
 }
 
-// Radices of n (4s first, then 2, 3, 5, other primes); false if a prime factor exceeds
+// Radices of n (8s first, then 9, 4, 2, 3, 5, other primes); false if a prime factor exceeds
 // FFT_PMAX or there are too many stages.
 static bool fft_plan(int n, FftPlan* p) {
   p->nf = 0;
-  const int pref[] = {4, 2, 3, 5};
+  const int pref[] = {8, 9, 4, 2, 3, 5};
   for (int r : pref)
     while (n % r == 0) {
       if (p->nf == FFT_MAXF) return false;
