@@ -10,7 +10,7 @@ network.  Each test grid is one seeded GRF slowness model with `--rhs` point sou
 solved to a 1e-6 relative residual.
 
     python -m paper_2306_17486_gb300.ablation [--steps S] [--sizes 128:16:3,256:32:3]
-        [--test 288:16:4,576:32:4,1152:64:5] [--rhs R] [--cnn-every K] [--out file.json]
+        [--test 288:16:4,576:32:4,1152:64:5] [--rhs R] [--cnn-every K] [--maxit M] [--out file.json]
 
 The JSON written to --out is rewritten after every phase, so an interrupted run keeps
 what it measured.
@@ -33,12 +33,12 @@ def _sizes(text: str):
     return tuple(tuple(int(v) for v in t.split(":")) for t in text.split(","))
 
 
-def solve_row(helm, p, b, net, cnn_every: int) -> dict:
+def solve_row(helm, p, b, net, cnn_every: int, maxit: int = 2000) -> dict:
     """One FGMRES(10) solve of the batch b; iteration statistics and ms per RHS."""
     helm.fgmres_solve(p, b, cnn=net, restart=10, rtol=1e-6, maxit=5, cnn_every=cnn_every)   # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, st = helm.fgmres_solve(p, b, cnn=net, restart=10, rtol=1e-6, maxit=2000, cnn_every=cnn_every)
+    _, st = helm.fgmres_solve(p, b, cnn=net, restart=10, rtol=1e-6, maxit=maxit, cnn_every=cnn_every)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     it = st["iters"].astype(np.float64)
@@ -54,6 +54,7 @@ def main():
     ap.add_argument("--test", default="288:16:4,576:32:4", help="test grids N_total:abl:levels")
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--cnn-every", type=int, default=1)
+    ap.add_argument("--maxit", type=int, default=2000, help="iteration cap of the test solves")
     ap.add_argument("--skip-threshold", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None)
@@ -65,8 +66,8 @@ def main():
     from . import train as T
 
     res = {"what": "implicit vs explicit U-Net (Section 6), equal training", "steps": a.steps, "batch": a.batch,
-           "train_sizes": a.sizes, "rhs": a.rhs, "cnn_every": a.cnn_every, "seed": a.seed, "train": {},
-           "test": []}
+           "train_sizes": a.sizes, "rhs": a.rhs, "cnn_every": a.cnn_every, "maxit": a.maxit, "seed": a.seed,
+           "train": {}, "test": []}
 
     def dump():
         if a.out:
@@ -92,10 +93,10 @@ def main():
         p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device="cuda"), abl,
                          2 * np.pi / (10.0 * float(kap.max())), levels=lv)
         b = torch.tensor(synth.random_point_sources(N, abl, a.rhs, seed=1000), dtype=torch.complex64, device="cuda")
-        row = {"grid": N, "abl": abl, "levels": lv, "mg_only": solve_row(helm, p, b, None, a.cnn_every)}
+        row = {"grid": N, "abl": abl, "levels": lv, "mg_only": solve_row(helm, p, b, None, a.cnn_every, a.maxit)}
         for name, net in nets.items():
             net.set_problem(p)
-            row[name] = solve_row(helm, p, b, net, a.cnn_every)
+            row[name] = solve_row(helm, p, b, net, a.cnn_every, a.maxit)
         res["test"].append(row)
         print(json.dumps(row), flush=True)
         dump()
