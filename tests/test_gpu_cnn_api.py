@@ -208,3 +208,34 @@ def test_trained_network_iteration_count_matches_the_oracle(helm):
                               rtol=1e-6, maxit=2000, warmup_iters=3, cnn_every=1, fallback=False)
     assert st["status"][0] == 1, st
     assert abs(int(st["iters"][0]) - n_oracle) <= 0.1 * n_oracle, (int(st["iters"][0]), n_oracle)
+
+
+def test_trainer_resume_is_bitwise(helm, tmp_path):
+    """A training run stopped, checkpointed (Trainer.save) and resumed in a fresh trainer
+    (Trainer.load) continues exactly as the uninterrupted run: parameters, BN running
+    statistics and Adam moments equal bit for bit (every reduction of the training path
+    runs in a fixed order, and the checkpoint holds both random generators' states)."""
+    from paper_2306_17486_gb300 import train as T
+
+    def fresh():
+        net = helm.Cnn(skip_threshold=256)
+        net.load_dict(synth.random_params(T.init_spec(net), seed=5))
+        tr = T.Trainer(net, sizes=((128, 16, 3),), batch=8, steps=6, seed=3, pool=4, kappas_per_batch=2)
+        return net, tr
+
+    net_a, tr_a = fresh()
+    tr_a.run(4, log=None)
+    ckpt = str(tmp_path / "ckpt.npz")
+    tr_a.save(ckpt)
+    tr_a.run(2, log=None)
+    torch.cuda.synchronize()
+    net_b, tr_b = fresh()
+    tr_b.load(ckpt)
+    tr_b.run(2, log=None)
+    torch.cuda.synchronize()
+    assert tr_b.step_i == tr_a.step_i == 6
+    assert torch.equal(net_a.params, net_b.params)
+    assert np.array_equal(net_a.running_dict_flat(), net_b.running_dict_flat())
+    assert torch.equal(tr_a.opt.m, tr_b.opt.m) and torch.equal(tr_a.opt.v, tr_b.opt.v)
+    # and the resumed run really trained: the parameters moved from the checkpoint
+    assert not np.array_equal(np.load(ckpt)["params"], net_b.params.cpu().numpy())
