@@ -445,6 +445,18 @@ int helm_datagen_pairs(const helm_problem* p, const void* x, const int* iters_de
                        int max_iters, int normalise, void* ws, size_t ws_bytes, void* stream);
 int helm_datagen_workspace_size(const helm_problem* p, int batch, int max_iters, size_t* bytes);
 
+/*
+ * Random vectors x of the training pairs (Section 4.3: a smooth random error plus noise):
+ *   x_b = f_b / RMS(f_b) + noise (n_b0 + i n_b1),  f_b = G w_b0 + i G w_b1,
+ * G the periodic Gaussian filter of standard deviation `sigma` cells along both axes
+ * (weights exp(-t^2 / (2 sigma^2)) for |t| <= ceil(3 sigma), normalised to sum 1), RMS
+ * over the grid.  white: device float [batch][4][n][n], the planes w_b0, w_b1, n_b0, n_b1
+ * of standard normal numbers drawn by the caller; x: device complex64 [batch][n][n]
+ * (written).  Stream-ordered, no workspace.  HELM_EINVAL unless 0 < sigma <= 8 and
+ * noise >= 0.
+ */
+int helm_training_field(const float* white, int batch, int n, float sigma, float noise, void* x, void* stream);
+
 /* Read and clear the device error word (HELM_DEVERR_* bits) of the current device. */
 int helm_device_errors(unsigned int* flags);
 

@@ -583,6 +583,21 @@ class CnnFunction(torch.autograd.Function):
         return g, None, None, None
 
 
+def training_field(white: torch.Tensor, sigma: float, noise: float) -> torch.Tensor:
+    """Random training vectors (Section 4.3): white is a float32 CUDA tensor [B, 4, n, n]
+    of standard normal numbers (planes w0, w1, n0, n1); returns complex64 [B, n, n]
+    x = f / RMS(f) + noise (n0 + i n1) with f the periodic Gaussian filter (std sigma
+    cells) of w0 + i w1."""
+    _need(white, torch.float32, "white")
+    if white.dim() != 4 or white.shape[1] != 4 or white.shape[2] != white.shape[3]:
+        raise ValueError("white must be [B, 4, n, n]")
+    B, n = white.shape[0], white.shape[2]
+    x = torch.empty((B, n, n), dtype=torch.complex64, device=white.device)
+    check(lib().helm_training_field(_ptr(white), B, n, float(sigma), float(noise), _ptr(x), _stream()),
+          "helm_training_field")
+    return x
+
+
 def datagen_pairs(p: Problem, x: torch.Tensor, iters: torch.Tensor, max_iters: int = 20, normalise: bool = True):
     """Eq. (17) on the device: (e, r) complex64 for random x [B, N, N] (complex64) and
     per-sample FGMRES iteration counts `iters` (int32 CUDA tensor)."""

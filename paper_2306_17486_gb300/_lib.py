@@ -60,6 +60,7 @@ PROTOS = {
     "helm_solver_plan_solve": (i32, [vp, vp, vp, vp]),
     "helm_solver_plan_destroy": (i32, [vp]),
     "helm_datagen_pairs": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp]),
+    "helm_training_field": (i32, [vp, i32, i32, C.c_float, C.c_float, vp, vp]),
     "helm_datagen_workspace_size": (i32, [vp, i32, i32, C.POINTER(sz)]),
     "helm_device_errors": (i32, [C.POINTER(C.c_uint)]),
     "helm_last_error_string": (C.c_char_p, []),

@@ -23,7 +23,105 @@ __global__ void k_pairs_finish(const float2* __restrict__ x, const double2* __re
   }
 }
 
+// ---- random training vectors (the x of Eq. 17) ------------------------------------
+// Periodic Gaussian filter of one real plane, one 32 x 32 output tile per CTA: the tile
+// plus a halo of RF cells is staged in shared memory (indices wrapped), filtered along
+// x into a second array, then along y.  Weights exp(-t^2 / (2 sigma^2)), |t| <= rad,
+// normalised to sum 1.  Plane p of sample b goes to component p of x (p = 0: real).
+constexpr int TF_T = 32;
+constexpr int TF_RMAX = 24;
+
+__global__ void __launch_bounds__(256) k_field_filter(const float* __restrict__ white, int n, float sigma, int rad,
+                                                      float* __restrict__ x) {
+  __shared__ float in[TF_T + 2 * TF_RMAX][TF_T + 2 * TF_RMAX];
+  __shared__ float hx[TF_T + 2 * TF_RMAX][TF_T];
+  __shared__ float wt[2 * TF_RMAX + 1];
+  const int b = blockIdx.z >> 1, plane = blockIdx.z & 1;
+  const int x0 = blockIdx.x * TF_T, y0 = blockIdx.y * TF_T;
+  const int span = TF_T + 2 * rad;
+  const float* src = white + (static_cast<long>(b) * 4 + plane) * n * n;
+  if (threadIdx.x == 0) {
+    float sum = 0.f;
+    for (int t = -rad; t <= rad; ++t) {
+      const float v = expf(-0.5f * (t / sigma) * (t / sigma));
+      wt[t + rad] = v;
+      sum += v;
+    }
+    for (int t = 0; t <= 2 * rad; ++t) wt[t] /= sum;
+  }
+  for (int i = threadIdx.x; i < span * span; i += blockDim.x) {
+    const int ly = i / span, lx = i - ly * span;
+    const int gy = ((y0 + ly - rad) % n + n) % n, gx = ((x0 + lx - rad) % n + n) % n;
+    in[ly][lx] = src[static_cast<long>(gy) * n + gx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < span * TF_T; i += blockDim.x) {
+    const int ly = i / TF_T, lx = i - ly * TF_T;
+    float acc = 0.f;
+    for (int t = 0; t <= 2 * rad; ++t) acc = fmaf(wt[t], in[ly][lx + t], acc);
+    hx[ly][lx] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < TF_T * TF_T; i += blockDim.x) {
+    const int ly = i / TF_T, lx = i - ly * TF_T;
+    const int gy = y0 + ly, gx = x0 + lx;
+    if (gy >= n || gx >= n) continue;
+    float acc = 0.f;
+    for (int t = 0; t <= 2 * rad; ++t) acc = fmaf(wt[t], hx[ly + t][lx], acc);
+    x[((static_cast<long>(b) * n + gy) * n + gx) * 2 + plane] = acc;
+  }
+}
+
+// x_b <- x_b / RMS(x_b) + noise (n0 + i n1), one CTA per sample (the sum of |x|^2 in a
+// fixed order: per-thread FP64 partials, then a tree over the CTA)
+__global__ void __launch_bounds__(1024) k_field_finish(const float* __restrict__ white, int n, float noise,
+                                                       float2* __restrict__ x) {
+  __shared__ double red[1024];
+  const int b = blockIdx.x;
+  const long nn = static_cast<long>(n) * n;
+  float2* xb = x + b * nn;
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+    const float2 v = xb[i];
+    acc += static_cast<double>(v.x) * v.x + static_cast<double>(v.y) * v.y;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double ms = red[0] / static_cast<double>(nn);
+  const float sc = ms > 0.0 ? static_cast<float>(1.0 / sqrt(ms)) : 0.f;
+  const float* n0 = white + (static_cast<long>(b) * 4 + 2) * nn;
+  const float* n1 = n0 + nn;
+  for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+    const float2 v = xb[i];
+    xb[i] = make_float2(fmaf(noise, n0[i], v.x * sc), fmaf(noise, n1[i], v.y * sc));
+  }
+}
+
 }  // namespace
+
+extern "C" int helm_training_field(const float* white, int batch, int n, float sigma, float noise, void* x,
+                                   void* stream) {
+  const int rad = static_cast<int>(ceilf(3.f * sigma));
+  if (!white || !x || batch <= 0 || n <= 0 || !(sigma > 0.f) || rad > TF_RMAX || !(noise >= 0.f)) {
+    helm::set_error("helm_training_field: invalid argument (sigma in (0, %d], noise >= 0)", TF_RMAX / 3);
+    return HELM_EINVAL;
+  }
+  if (batch > 65535 / 2) {
+    helm::set_error("helm_training_field: batch %d too large", batch);
+    return HELM_ESHAPE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  dim3 grid(helm::div_up(n, TF_T), helm::div_up(n, TF_T), 2 * batch);
+  HELM_LAUNCH("k_field_filter", st, k_field_filter<<<grid, 256, 0, st>>>(white, n, sigma, rad, static_cast<float*>(x)));
+  HELM_CHECK_LAUNCH("k_field_filter");
+  HELM_LAUNCH("k_field_finish", st, k_field_finish<<<batch, 1024, 0, st>>>(white, n, noise, static_cast<float2*>(x)));
+  HELM_CHECK_LAUNCH("k_field_finish");
+  return HELM_OK;
+}
 
 extern "C" int helm_datagen_pairs(const helm_problem* p, const void* x_, const int* iters_dev, void* e_, void* r_,
                                   int batch, int max_iters, int normalise, void* ws, size_t ws_bytes, void* stream) {

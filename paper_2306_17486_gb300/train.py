@@ -26,35 +26,18 @@ import time
 
 import numpy as np
 import torch
-import torch.nn.functional as F
 
-from . import Adam, Cnn, Problem, datagen_pairs, mse_loss
-
-
-def _gauss1d(sigma: float, device) -> torch.Tensor:
-    r = int(math.ceil(3 * sigma))
-    t = torch.arange(-r, r + 1, dtype=torch.float32, device=device)
-    k = torch.exp(-0.5 * (t / sigma) ** 2)
-    return k / k.sum()
+from . import Adam, Cnn, Problem, datagen_pairs, mse_loss, training_field
 
 
 def smooth_plus_noise(B: int, N: int, gen: torch.Generator, ell: float = 4.0, noise: float = 0.1,
                       device="cuda") -> torch.Tensor:
     """Random training vectors: complex Gaussian random field (Gaussian filter of std
-    ell/sqrt(2), periodic) scaled to unit RMS, plus `noise` x complex white noise."""
-    k = _gauss1d(ell / math.sqrt(2.0), device)
-    r = k.numel() // 2
-    w = torch.randn((2 * B, 1, N, N), generator=gen, device=device)
-    w = F.pad(w, (r, r, 0, 0), mode="circular")
-    w = F.conv2d(w, k.view(1, 1, 1, -1))
-    w = F.pad(w, (0, 0, r, r), mode="circular")
-    w = F.conv2d(w, k.view(1, 1, -1, 1))
-    w = w.view(B, 2, N, N)
-    f = torch.complex(w[:, 0], w[:, 1])
-    f = f / torch.sqrt((f.abs() ** 2).mean(dim=(1, 2), keepdim=True))
-    nz = torch.complex(torch.randn((B, N, N), generator=gen, device=device),
-                       torch.randn((B, N, N), generator=gen, device=device))
-    return (f + noise * nz).to(torch.complex64).contiguous()
+    ell/sqrt(2), periodic) scaled to unit RMS, plus `noise` x complex white noise.  The
+    standard normal numbers are drawn here; the filter, scaling and sum run in the
+    library (helm_training_field)."""
+    white = torch.randn((B, 4, N, N), generator=gen, device=device)
+    return training_field(white, ell / math.sqrt(2.0), noise)
 
 
 class Trainer:

@@ -213,3 +213,32 @@ def test_network_forward_at_the_benchmark_shape(helm):
         err = np.linalg.norm(e[i] - ref[0]) / np.linalg.norm(ref[0])
         print(f"sample {i}: 2-norm relative error {err:.2e}")
         assert err < 4e-2, (i, err)
+
+
+@pytest.mark.parametrize("B,n,sigma", [(3, 40, 4 / np.sqrt(2.0)), (2, 70, 2.0)])
+def test_training_field_matches_its_definition(helm, B, n, sigma):
+    """helm_training_field against a plain evaluation of its definition: the periodic
+    Gaussian filter with the discrete weights exp(-t^2 / 2 sigma^2), |t| <= ceil(3 sigma),
+    normalised to sum 1, along both axes, each sample scaled to unit RMS, plus noise."""
+    rng = np.random.default_rng(n)
+    white = rng.standard_normal((B, 4, n, n)).astype(np.float32)
+    x = helm.training_field(torch.tensor(white, device="cuda"), sigma, 0.1).cpu().numpy()
+    rad = int(np.ceil(3 * sigma))
+    t = np.arange(-rad, rad + 1)
+    w = np.exp(-0.5 * (t / sigma) ** 2)
+    w /= w.sum()
+    wd = white.astype(np.float64)
+
+    def filt(a):
+        out = np.zeros_like(a)
+        for k, wk in zip(t, w):
+            out += wk * np.roll(a, -k, axis=1)
+        out2 = np.zeros_like(a)
+        for k, wk in zip(t, w):
+            out2 += wk * np.roll(out, -k, axis=0)
+        return out2
+
+    for b in range(B):
+        f = filt(wd[b, 0]) + 1j * filt(wd[b, 1])
+        ref = f / np.sqrt(np.mean(np.abs(f) ** 2)) + 0.1 * (wd[b, 2] + 1j * wd[b, 3])
+        assert np.max(np.abs(x[b] - ref)) <= 1e-5 * np.max(np.abs(ref)), np.max(np.abs(x[b] - ref))
