@@ -45,13 +45,15 @@ LEVELS = {288: 4, 576: 4, 1152: 5, 2304: 6}   # coarsest grids 36^2, 72^2, 72^2,
 def bucket_config(n: int):
     """Grid of interior size n: absorbing layer max(16, n/16) cells per side (N = 288,
     576, 1152, 2304 for n = 256 ... 2048), the V-cycle depth of the benchmark workloads
-    (other sizes: the coarsest grid at most 72^2), iteration cap."""
+    (other sizes: deepened until the coarsest grid is at most 72^2 or N cannot be halved
+    again), iteration cap."""
     abl = max(16, n // 16)
     N = n + 2 * abl
     levels = LEVELS.get(N)
     if levels is None:
+        # deepen while the coarsest grid is above 72^2 and the next level still divides N
         levels = 2
-        while levels < 8 and ((N >> (levels - 1)) > 72 or N % (1 << levels)):
+        while levels < 8 and (N >> (levels - 1)) > 72 and N % (1 << levels) == 0:
             levels += 1
     maxit = 2000 if N <= 600 else (4000 if N <= 1200 else 8000)
     return N, abl, levels, maxit
