@@ -27,6 +27,10 @@ Architecture (c0 = 16, expansion t = 6; readings where the paper is silent):
   Implicit kernels initialised to L + iI (Section 5.3).
   Explicit U-Net (Section 6, the comparison network): the same encoder-solver network
   without the implicit step at the coarsest level (implicit=False below).
+  Rectangular grids (the out-of-distribution shapes of Section 5.1; the paper trains on
+  squares): an H x W grid runs every layer per axis, the coarsest map is m_y x m_x with
+  its Green's function on the per-axis grids, and the last downsampling is skipped when
+  the shorter side is below 512.
 """
 from __future__ import annotations
 
@@ -330,7 +334,7 @@ def implicit_layer(tp: Tape, x: Var, kname: str, ghat: np.ndarray) -> Var:
         gy = out.g[:, :nk] + 1j * out.g[:, nk:]
         gx = np.stack([imp.implicit_adjoint(gy[:, k], ghat[k]) for k in range(nk)], axis=1)
         x.acc(np.concatenate([gx.real, gx.imag], axis=1))
-        m = x.a.shape[-1]
+        m = x.a.shape[-2:]
         K = tp.params[kname]
         gK = np.zeros_like(K)
         for k in range(nk):
@@ -355,6 +359,13 @@ def skip_last_down(I: int, threshold: int = 512) -> bool:
 def coarsest_size(I: int, skip: bool | None = None) -> int:
     skip = skip_last_down(I) if skip is None else skip
     return I // 8 if skip else I // 16
+
+
+def coarsest_shape(H: int, W: int, skip: bool | None = None) -> tuple[int, int]:
+    """(m_y, m_x) of an H x W grid.  The paper's grids are square; on a rectangle the
+    last downsampling is skipped when the shorter side is below the threshold."""
+    skip = skip_last_down(min(H, W)) if skip is None else skip
+    return coarsest_size(H, skip), coarsest_size(W, skip)
 
 
 def build_ghat(params, m: int, literal: bool = False) -> np.ndarray:
@@ -439,14 +450,15 @@ class Network:
 
     def forward(self, r: np.ndarray, kfeat: np.ndarray, train: bool = False,
                 skip: bool | None = None, record: bool = False):
-        """e = s * Net(r / s), s = RMS of r over the grid, for a batch r [B, I, I] complex
+        """e = s * Net(r / s), s = RMS of r over the grid, for a batch r [B, H, W] complex
         (the paper leaves the scale unstated; the RMS is this implementation's choice).
+        The paper's grids are square (H = W); a rectangle runs every layer per axis.
 
         Returns (e, tape, scale); the tape's backward accumulates parameter
         gradients in tape.grads given the complex gradient of the loss w.r.t. e.
         """
-        B, I, _ = r.shape
-        skip = skip_last_down(I) if skip is None else skip
+        B, H, W = r.shape
+        skip = skip_last_down(min(H, W)) if skip is None else skip
         # s is the residual's RMS over the grid, so the network sees O(1)
         # values at every grid size (the multiscale setting of Section 4.3)
         s = np.sqrt((np.abs(r) ** 2).reshape(B, -1).mean(axis=1))
@@ -459,7 +471,9 @@ class Network:
         running = self.running if train else self.running
         kf = Var(kfeat)
         encs = encoder(tp, kf, train, running)
-        m = coarsest_size(I, skip)
+        m = coarsest_shape(H, W, skip)
+        if m[0] == m[1]:
+            m = m[0]
         p = solver(tp, x0, encs, self.ghat(m) if self.implicit else None, train, running, skip)
         pc = p.a[:, 0] + 1j * p.a[:, 1]
         e = prolong(pc) * s[:, None, None]

@@ -275,3 +275,44 @@ def test_network_input_gradient_matches_central_differences(train):
         assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-12 * abs(L)), (fd, an)
     euler = float(np.real(np.vdot(gr, r)))
     assert abs(euler - float(np.real(np.vdot(ge, e)))) <= 1e-10 * np.abs(gr).sum() * np.abs(r).max()
+
+
+def _transposed_params(P):
+    """Every 3x3 kernel transposed (convolutions, transposed convolutions, depthwise
+    and the implicit kernels); 1x1 weights, biases and BN parameters unchanged."""
+    return {k: (np.swapaxes(v, -1, -2).copy() if v.ndim >= 3 and v.shape[-2:] == (3, 3) else v)
+            for k, v in P.items()}
+
+
+@pytest.mark.parametrize("H,W,skip", [(32, 48, True), (32, 64, False)])
+@pytest.mark.parametrize("train", [False, True])
+def test_rectangular_network_transposes_with_its_kernels(H, W, skip, train):
+    """An H x W grid (the out-of-distribution shapes of Section 5.1 are rectangles).
+    With every 3x3 kernel transposed, the network maps r^T to e^T: the fixed R and P,
+    BatchNorm and softplus commute with the transpose.  A height used for a width
+    anywhere on the path (a shape, a crop, an axis of the Green's function) breaks it."""
+    c0 = 4
+    P = synth.random_params(cnn.param_spec(c0), seed=5, bn_jitter=0.2)
+    K = P["s.imp.K"]
+    K[:, :, 0, 1] += 0.5          # asymmetric implicit kernels
+    net = cnn.Network(P, c0=c0)
+    netT = cnn.Network(_transposed_params(P), c0=c0)
+    rng = np.random.default_rng(6)
+    kf = rng.uniform(0.0625, 1.0, size=(1, 2, H, W))
+    r = synth.random_complex((2, H, W), 7)
+    e, _ = net.forward(r, kf, train=train, skip=skip)
+    assert e.shape == (2, H, W)
+    eT, _ = netT.forward(np.swapaxes(r, -1, -2).copy(), np.swapaxes(kf, -1, -2).copy(), train=train, skip=skip)
+    assert np.abs(eT - np.swapaxes(e, -1, -2)).max() <= 1e-12 * np.abs(e).max()
+    # not a symmetry of the untransposed network: the kernels matter
+    e2, _ = net.forward(np.swapaxes(r, -1, -2).copy(), np.swapaxes(kf, -1, -2).copy(), train=train, skip=skip)
+    assert np.abs(e2 - np.swapaxes(e, -1, -2)).max() > 1e-3 * np.abs(e).max()
+
+
+def test_rectangular_coarsest_shape_and_skip_rule():
+    """The coarsest map is m_y x m_x (I/16 per axis, or I/8 with the last downsampling
+    skipped, Section 5.3); a rectangle skips it when its shorter side is below 512."""
+    assert cnn.coarsest_shape(576, 1088) == (36, 68)
+    assert cnn.coarsest_shape(448, 896) == (56, 112)
+    assert cnn.coarsest_shape(512, 512) == (cnn.coarsest_size(512),) * 2
+    assert cnn.coarsest_shape(256, 256) == (cnn.coarsest_size(256),) * 2

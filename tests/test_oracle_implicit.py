@@ -115,3 +115,104 @@ def test_kernel_gradient_matches_finite_differences(literal):
             fd = (loss(Kp) - loss(Km)) / (2 * h)
             an = gK[idx].real if part == "re" else gK[idx].imag
             assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-8), (idx, part, fd, an)
+
+
+# ---- rectangular coarsest maps (m_y x m_x): every size of Eq. (14)-(15) per axis -----
+
+def _greens_hat_brute(K, my, mx, eps=imp.EPS):
+    """G_hat of an m_y x m_x map with explicit DFT sums and no FFT: K_hat on the
+    6m_y x 6m_x periodic grid from the nine taps, the Tikhonov quotient, G at the
+    2m_y x 2m_x offsets around the source, then the 2D DFT of the cropped window."""
+    ny, nx = 6 * my, 6 * mx
+    u = np.arange(ny)[:, None]
+    v = np.arange(nx)[None, :]
+    Kh = np.zeros((ny, nx), complex)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            Kh += K[a + 1, b + 1] * np.exp(-2j * np.pi * (a * u / ny + b * v / nx))
+    H = np.conj(Kh) / (np.abs(Kh) ** 2 + eps)
+    dy = [i if i < my else i - 2 * my for i in range(2 * my)]
+    dx = [j if j < mx else j - 2 * mx for j in range(2 * mx)]
+    Gc = np.zeros((2 * my, 2 * mx), complex)
+    for i, di in enumerate(dy):
+        for j, dj in enumerate(dx):
+            # the source sits at (3m_y, 3m_x): G there + offset d is the inverse DFT at d
+            Gc[i, j] = (H * np.exp(2j * np.pi * (u * di / ny + v * dj / nx))).sum() / (ny * nx)
+    p = np.arange(2 * my)[:, None]
+    q = np.arange(2 * mx)[None, :]
+    Gh = np.zeros_like(Gc)
+    for i in range(2 * my):
+        for j in range(2 * mx):
+            Gh += Gc[i, j] * np.exp(-2j * np.pi * (p * i / (2 * my) + q * j / (2 * mx)))
+    return Gh
+
+
+def test_rectangular_green_hat_matches_brute_force_sums():
+    K = imp.laplacian_plus_i() + 0.25 * synth.random_complex((3, 3), 20)
+    for my, mx in ((2, 3), (3, 2)):
+        assert np.allclose(imp.greens_hat(K, (my, mx)), _greens_hat_brute(K, my, mx), atol=1e-12)
+
+
+def test_rectangular_green_and_layer_transpose_with_the_kernel():
+    """Transposing the kernel transposes G_hat of the transposed map, and Eq. (14) on
+    the transposed input gives the transposed output: an exchanged axis fails here."""
+    K = imp.laplacian_plus_i() + 0.3 * synth.random_complex((3, 3), 21)
+    K[0, 1] += 0.4    # an asymmetric kernel: K != K^T
+    my, mx = 3, 5
+    Gh = imp.greens_hat(K, (my, mx))
+    assert Gh.shape == (2 * my, 2 * mx)
+    GhT = imp.greens_hat(K.T, (mx, my))
+    assert np.allclose(GhT, Gh.T, atol=1e-13)
+    assert not np.allclose(imp.greens_hat(K, (mx, my)), GhT, atol=1e-6)
+    x = synth.random_complex((2, my, mx), 22)
+    y = imp.implicit_apply(x, Gh)
+    yT = imp.implicit_apply(np.swapaxes(x, -1, -2), GhT)
+    assert np.allclose(yT, np.swapaxes(y, -1, -2), atol=1e-13)
+
+
+def test_rectangular_implicit_apply_is_linear_convolution_with_cropped_green():
+    my, mx = 3, 5
+    K = imp.laplacian_plus_i() + 0.2 * synth.random_complex((3, 3), 23)
+    Ghat = imp.greens_hat(K, (my, mx))
+    Gc = np.fft.ifft2(Ghat)
+    x = synth.random_complex((my, mx), 24)
+    y = imp.implicit_apply(x, Ghat)
+    ref = np.zeros((my, mx), complex)
+    for i in range(my):
+        for j in range(mx):
+            for p in range(my):
+                for q in range(mx):
+                    ref[i, j] += Gc[(i - p) % (2 * my), (j - q) % (2 * mx)] * x[p, q]
+    assert np.allclose(y, ref, atol=1e-13)
+    # the uncropped G inverts K on the periodic grid up to the eps regularisation
+    G, *_ = imp.greens_raw(K, (my, mx))
+    KG = np.zeros_like(G)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            KG += K[a + 1, b + 1] * np.roll(np.roll(G, a, axis=0), b, axis=1)
+    delta = np.zeros_like(KG)
+    delta[3 * my, 3 * mx] = 1
+    assert np.abs(KG - delta).max() < 1e-4
+
+
+def test_rectangular_adjoint_and_kernel_gradient():
+    my, mx = 3, 4
+    K = imp.laplacian_plus_i() + 0.3 * synth.random_complex((3, 3), 25)
+    Ghat = imp.greens_hat(K, (my, mx))
+    x = synth.random_complex((2, my, mx), 26)
+    w = synth.random_complex((2, my, mx), 27)
+    assert np.isclose(np.vdot(imp.implicit_apply(x, Ghat), w), np.vdot(x, imp.implicit_adjoint(w, Ghat)),
+                      rtol=1e-12)
+
+    def loss(Kc):
+        return float(np.real(np.vdot(w, imp.implicit_apply(x, imp.greens_hat(Kc, (my, mx))))))
+
+    gK = imp.greens_backward(K, (my, mx), imp.implicit_grad_ghat(x, w))
+    h = 1e-6
+    for idx in [(0, 1), (1, 1), (2, 0)]:
+        for unit in (1.0, 1j):
+            Kp = K.copy(); Kp[idx] += h * unit
+            Km = K.copy(); Km[idx] -= h * unit
+            fd = (loss(Kp) - loss(Km)) / (2 * h)
+            an = gK[idx].real if unit == 1.0 else gK[idx].imag
+            assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-8), (idx, unit, fd, an)
