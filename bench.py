@@ -12,10 +12,12 @@ The same line carries `workload_1152`: the 1024^2 grid (plus a 64-cell layer, 11
 nodes, 5-level V-cycle), 2 slowness models x 16 point sources, each arm timed once; and
 `serving`: p50/p99 latency of a burst of mixed-size requests (288^2, 576^2, 1152^2
 nodes, 8 right-hand sides each) served by captured solver plans, with and without the
-network.
+network; and `ood_shapes`: the trained network against SL-MG alone on the rectangular
+out-of-distribution shapes of Section 5.1 (512 x 1024 and 352 x 800 interiors, 8 point
+sources each).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--skip-1152]
-        [--skip-serving]
+        [--skip-serving] [--skip-ood]
         (N > 1: launched by torchrun, one replica per GPU, independent models per rank)
 """
 from __future__ import annotations
@@ -244,6 +246,51 @@ def run_1152(helm, net, dev, rank: int):
     return out
 
 
+# The out-of-distribution grid shapes of Section 5.1 (512 x 1024 and 352 x 800 interiors,
+# rows x columns) with a 32-cell absorbing layer: synthetic stand-ins for its models
+# (a layered + GRF field and a salt body), one model and OOD_RHS point sources each
+OOD_SHAPES = ((512, 1024, "layered_grf"), (352, 800, "salt"))
+OOD_ABL, OOD_LEVELS, OOD_RHS = 32, 4, 8
+
+
+def run_ood(helm, net, dev, rank: int):
+    """ms per RHS and iterations to 1e-6 on the rectangular out-of-distribution shapes:
+    the trained network (on every CNN_EVERY-th step) against SL-MG alone; one timed pass
+    per arm after an untimed warm-up solve, inputs resident in HBM."""
+    import torch
+    import synth
+    out = {"abl": OOD_ABL, "mg_levels": OOD_LEVELS, "rhs_per_model": OOD_RHS, "grids": []}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k, (h, w, kind) in enumerate(OOD_SHAPES):
+        kap = synth.rect_kappa(h, w, OOD_ABL, seed=40 + 2 * rank + k, kind=kind)
+        oh = 2.0 * np.pi / (10.0 * float(kap.max()))
+        p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device=dev), OOD_ABL, oh, levels=OOD_LEVELS)
+        b = torch.tensor(synth.rect_point_sources(h, w, OOD_ABL, OOD_RHS, seed=4000 + 2 * rank + k),
+                         dtype=torch.complex64, device=dev)
+        x = torch.zeros(b.shape, dtype=torch.complex128, device=dev)
+        p.workspace(OOD_RHS, RESTART, net)
+        net.set_problem(p)
+        rec = {"grid": [h + 2 * OOD_ABL, w + 2 * OOD_ABL], "interior": [h, w], "model": kind}
+        for name, cnn in (("cnn_mg", True), ("mg_only", False)):
+            helm.fgmres_solve(p, b, x, cnn=net if cnn else None, restart=RESTART, rtol=RTOL, maxit=30,
+                              warmup_iters=3, cnn_every=CNN_EVERY)
+            x.zero_()
+            torch.cuda.synchronize()
+            e0.record()
+            _, st = helm.fgmres_solve(p, b, x, cnn=net if cnn else None, restart=RESTART, rtol=RTOL, maxit=MAXIT,
+                                      warmup_iters=3, cnn_every=CNN_EVERY)
+            e1.record()
+            torch.cuda.synchronize()
+            rec[name] = {"ms_per_rhs": round(e0.elapsed_time(e1) / OOD_RHS, 3),
+                         "iterations_mean": round(float(st["iters"].mean()), 1),
+                         "converged_frac": float(np.mean(st["status"] == 1)),
+                         "max_true_rel_res": float(st["rel_res_true"].max())}
+        rec["speedup_vs_mg_only"] = round(rec["mg_only"]["ms_per_rhs"] / rec["cnn_mg"]["ms_per_rhs"], 3)
+        out["grids"].append(rec)
+        del p
+    return out
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     import __graft_entry__
@@ -407,6 +454,8 @@ def run_gpu(args, rank: int, world: int):
         out["workload_1152"] = run_1152(helm, net, dev, rank)
     if not args.skip_serving:
         out["serving"] = run_serving()
+    if not args.skip_ood:
+        out["ood_shapes"] = run_ood(helm, net, dev, rank)
     out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
     out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
     if rank == 0:
@@ -668,6 +717,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--skip-1152", action="store_true", help="leave out the 1152^2 (1024^2 interior) workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the mixed-size serving run")
+    ap.add_argument("--skip-ood", action="store_true",
+                    help="leave out the rectangular out-of-distribution shapes (512 x 1024, 352 x 800)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

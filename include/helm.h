@@ -290,6 +290,16 @@ int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const float* w_e
  */
 int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat, void* y, void* stream);
 
+/*
+ * The same layer on an m_y x m_x map (the coarsest map of a rectangular grid; the paper's
+ * grids are square, its out-of-distribution models of Section 5.1 are rectangles): x, y
+ * BF16 NHWC [batch][my][mx][c], each complex channel zero-padded to 2m_y x 2m_x, and
+ * ghat complex64 [c/2][2my][2mx] (helm_cnn_get_ghat_rect).  HELM_ESHAPE when the map
+ * exceeds shared memory or 2m_x or 2m_y has a prime factor above 17.
+ */
+int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y,
+                            void* stream);
+
 /* Launch-shape tuning table (process-wide, read at launch time; captured solver plans
  * keep the shapes they were captured with).  A knob's value for a layer of height
  * `height` run on `batch` images overrides the kernel family's launch heuristic.
@@ -358,11 +368,15 @@ int helm_cnn_get_running(helm_cnn* c, float* out_dev, void* stream);
 
 /* Run the encoder (evaluation-mode BN) on problem p's slowness model and cache the
  * encodings (Section 4.1: once per slowness model, reused for every RHS and
- * iteration).  Needed again after helm_cnn_set_params. */
+ * iteration).  Needed again after helm_cnn_set_params.  The grid may be a rectangle
+ * (ny x nx, both sides divisible by 16) for inference (set_problem, apply with train = 0,
+ * the composed preconditioner): every layer then runs per axis, the coarsest map is
+ * m_y x m_x, and the solver's last downsampling is skipped when the shorter side is below
+ * the skip threshold.  Training needs a square grid (HELM_ESHAPE otherwise). */
 int helm_cnn_set_problem(helm_cnn* c, const helm_problem* p, void* ws, size_t ws_bytes, void* stream);
 
 /* e = s Net(r / s), s = RMS of r over the grid (Eq. 16's SolverNet with the residual
- * normalisation of this library), r, e complex64 [batch][N][N].  train = 0: evaluation-mode BN with the
+ * normalisation of this library), r, e complex64 [batch][ny][nx].  train = 0: evaluation-mode BN with the
  * cached encodings.  train = 1: batch-statistics BN, encoder run on p in training mode
  * inside the call, activations saved in `ws` for helm_cnn_precond_backward, running
  * statistics updated (momentum 0.1). */
@@ -428,6 +442,10 @@ int helm_cnn_load(helm_cnn* c, const char* path, float* params_dev, void* stream
 /* Copy G_hat (Eq. 15, after crop and DFT) for coarsest size m to out_dev, complex64
  * [nk][2m][2m]; builds it if needed.  HELM_ESTATE for an explicit U-Net. */
 int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream);
+/* The same for an m_y x m_x coarsest map: complex64 [nk][2my][2mx], Eq. 15 on the
+ * 6m_y x 6m_x periodic grid.  Rectangular G_hat are derived on demand and not stored by
+ * helm_cnn_save. */
+int helm_cnn_get_ghat_rect(helm_cnn* c, int my, int mx, void* out_dev, void* stream);
 
 /* The composed preconditioner of Section 4.1: z = e + V(r - A e), e = s Net(r/s), s = RMS(r). */
 int helm_cnn_precond_apply(const helm_problem* p, helm_cnn* c, const void* r, void* z, int batch, void* ws,

@@ -441,11 +441,17 @@ class Cnn:
         self.running.copy_(torch.as_tensor(np.asarray(flat, dtype=np.float32)))
         check(lib().helm_cnn_set_running(self.handle, _ptr(self.running), _stream()), "set_running")
 
-    def ghat(self, m: int) -> torch.Tensor:
+    def ghat(self, m) -> torch.Tensor:
+        """G_hat (Eq. 15 after crop and DFT) of a coarsest map of side m, or of an
+        m_y x m_x map given as a pair: complex64 [nk, 2 m_y, 2 m_x]."""
+        my, mx = (m, m) if np.ndim(m) == 0 else (int(m[0]), int(m[1]))
         shapes = dict((n, s) for n, s, _ in self.spec)
         nk = shapes["s.imp.K"][1] if "s.imp.K" in shapes else 1   # explicit U-Net: the call fails
-        out = torch.empty((nk, 2 * m, 2 * m), dtype=torch.complex64, device=self.device)
-        check(lib().helm_cnn_get_ghat(self.handle, m, _ptr(out), _stream()), "get_ghat")
+        out = torch.empty((nk, 2 * my, 2 * mx), dtype=torch.complex64, device=self.device)
+        if my == mx:
+            check(lib().helm_cnn_get_ghat(self.handle, my, _ptr(out), _stream()), "get_ghat")
+        else:
+            check(lib().helm_cnn_get_ghat_rect(self.handle, my, mx, _ptr(out), _stream()), "get_ghat_rect")
         return out
 
     # ---- application ------------------------------------------------------------

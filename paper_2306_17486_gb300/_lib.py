@@ -73,6 +73,7 @@ PROTOS = {
                               vp]),
     "helm_ib_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     "helm_implicit_bf16": (i32, [vp, i32, i32, i32, vp, vp, vp]),
+    "helm_implicit_rect_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
     "helm_cnn_create": (i32, [C.POINTER(CnnDesc), C.POINTER(vp)]),
     "helm_cnn_destroy": (i32, [vp]),
     "helm_cnn_num_params": (i32, [vp, C.POINTER(sz)]),
@@ -84,6 +85,7 @@ PROTOS = {
     "helm_cnn_get_running": (i32, [vp, vp, vp]),
     "helm_cnn_set_problem": (i32, [vp, vp, vp, sz, vp]),
     "helm_cnn_get_ghat": (i32, [vp, i32, vp, vp]),
+    "helm_cnn_get_ghat_rect": (i32, [vp, i32, i32, vp, vp]),
     "helm_cnn_apply": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp]),
     "helm_cnn_precond_apply": (i32, [vp, vp, vp, vp, i32, vp, sz, vp]),
     "helm_cnn_precond_backward": (i32, [vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]),

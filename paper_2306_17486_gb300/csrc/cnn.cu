@@ -98,7 +98,7 @@ size_t packed_elems(const helm_cnn* c, const ParamInfo& pi) {
   return 0;
 }
 
-int skip_for(const helm_cnn* c, int I) { return I < c->desc.skip_threshold ? 1 : 0; }
+int skip_for(const helm_cnn* c, int H, int W) { return std::min(H, W) < c->desc.skip_threshold ? 1 : 0; }
 
 static Layer conv_layer(const helm_cnn* c, const std::string& w, const std::string& bn, int mode, int in, int out,
                         int add1, int add2, int act = 1) {
@@ -127,19 +127,21 @@ static Layer conv_layer(const helm_cnn* c, const std::string& w, const std::stri
   return L;
 }
 
-void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, int Bk) {
+void build_encoder_plan(const helm_cnn* c, int Hg, int Wg, Plan* pl, int* outs, int* kf, int Bk) {
   *pl = Plan();
-  pl->I = I;
+  pl->H = Hg;
+  pl->W = Wg;
   pl->B = Bk;
   const int C[3] = {c->desc.c0, 2 * c->desc.c0, 4 * c->desc.c0};
-  *kf = pl->add_tensor(Bk, I, I, 2);
-  int x = *kf, H = I;
+  *kf = pl->add_tensor(Bk, Hg, Wg, 2);
+  int x = *kf, H = Hg, W = Wg;
   for (int k = 0; k < 3; ++k) {
     H /= 2;
+    W /= 2;
     const std::string p = "e.dm" + std::to_string(k + 1);
-    const int a = pl->add_tensor(Bk, H, H, C[k]);
-    const int b = pl->add_tensor(Bk, H, H, C[k]);
-    const int o = pl->add_tensor(Bk, H, H, C[k]);
+    const int a = pl->add_tensor(Bk, H, W, C[k]);
+    const int b = pl->add_tensor(Bk, H, W, C[k]);
+    const int o = pl->add_tensor(Bk, H, W, C[k]);
     pl->layers.push_back(conv_layer(c, p + ".conv0.w", p + ".bn0", HELM_CONV_S2, x, a, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv1.w", p + ".bn1", HELM_CONV_S1, a, b, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv2.w", p + ".bn2", HELM_CONV_S1, b, o, -1, -1));
@@ -148,33 +150,36 @@ void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, 
   }
 }
 
-void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
+void build_solver_plan(const helm_cnn* c, int Hg, int Wg, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
                        int Bk, bool fuse_ib) {
   *pl = Plan();
-  pl->I = I;
+  pl->H = Hg;
+  pl->W = Wg;
   pl->B = B;
   pl->skip = skip;
   const int t = c->desc.expansion;
   const int C[3] = {c->desc.c0, 2 * c->desc.c0, 4 * c->desc.c0};
-  int H = I / 2;
-  *x0 = pl->add_tensor(B, H, H, 2);
+  int H = Hg / 2, W = Wg / 2;
+  *x0 = pl->add_tensor(B, H, W, 2);
   // encodings live in the encoder's arena: placeholders, resolved at run time
   for (int k = 0; k < 3; ++k) {
-    const int h = I >> (k + 1);
-    TensorDesc d{Bk, h, h, C[k], ~size_t(0)};
+    TensorDesc d{Bk, Hg >> (k + 1), Wg >> (k + 1), C[k], ~size_t(0)};
     pl->t.push_back(d);
     enc_ids[k] = static_cast<int>(pl->t.size()) - 1;
   }
   int x = *x0;
   int g[3];
   for (int k = 0; k < 3; ++k) {
-    if (k > 0) H /= 2;
+    if (k > 0) {
+      H /= 2;
+      W /= 2;
+    }
     const std::string p = "s.l" + std::to_string(k + 1);
-    const int f = pl->add_tensor(B, H, H, C[k]);
+    const int f = pl->add_tensor(B, H, W, C[k]);
     pl->layers.push_back(conv_layer(c, p + ".conv.w", p + ".bn", k == 0 ? HELM_CONV_S1 : HELM_CONV_S2, x, f, -1,
                                     enc_ids[k]));
     if (fuse_ib) {
-      g[k] = pl->add_tensor(B, H, H, C[k]);
+      g[k] = pl->add_tensor(B, H, W, C[k]);
       Layer ib = conv_layer(c, p + ".ib.exp.w", p + ".ib.bn0", HELM_CONV_S1, f, g[k], -1, -1);
       ib.kind = L_IB;
       ib.wp_dw = c->pidx.at(p + ".ib.dw.w");
@@ -185,9 +190,9 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
       x = g[k];
       continue;
     }
-    const int a = pl->add_tensor(B, H, H, t * C[k]);
-    const int d = pl->add_tensor(B, H, H, t * C[k]);
-    g[k] = pl->add_tensor(B, H, H, C[k]);
+    const int a = pl->add_tensor(B, H, W, t * C[k]);
+    const int d = pl->add_tensor(B, H, W, t * C[k]);
+    g[k] = pl->add_tensor(B, H, W, C[k]);
     pl->layers.push_back(conv_layer(c, p + ".ib.exp.w", p + ".ib.bn0", HELM_CONV_S1, f, a, -1, -1));
     Layer dw{};
     dw.kind = L_DW;
@@ -202,17 +207,19 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
     pl->layers.push_back(conv_layer(c, p + ".ib.proj.w", p + ".ib.bn2", HELM_CONV_S1, d, g[k], f, -1, 0));
     x = g[k];
   }
-  const int m = skip ? H : H / 2;
-  pl->m = m;
-  const int l4a = pl->add_tensor(B, m, m, C[2]);
-  const int l4b = pl->add_tensor(B, m, m, C[2]);
-  const int l4c = pl->add_tensor(B, m, m, C[2]);
+  const int my = skip ? H : H / 2, mx = skip ? W : W / 2;
+  pl->my = my;
+  pl->mx = mx;
+  pl->m = my;
+  const int l4a = pl->add_tensor(B, my, mx, C[2]);
+  const int l4b = pl->add_tensor(B, my, mx, C[2]);
+  const int l4c = pl->add_tensor(B, my, mx, C[2]);
   pl->layers.push_back(conv_layer(c, "s.l4.conv0.w", "s.l4.bn0", skip ? HELM_CONV_S1 : HELM_CONV_S2, x, l4a, -1, -1));
   pl->layers.push_back(conv_layer(c, "s.l4.conv1.w", "s.l4.bn1", HELM_CONV_S1, l4a, l4b, -1, -1));
   pl->layers.push_back(conv_layer(c, "s.l4.conv2.w", "s.l4.bn2", HELM_CONV_S1, l4b, l4c, -1, -1));
   x = l4c;
   if (!c->desc.explicit_unet) {
-    const int imp = pl->add_tensor(B, m, m, C[2]);
+    const int imp = pl->add_tensor(B, my, mx, C[2]);
     Layer li{};
     li.kind = L_IMPL;
     li.wparam = c->pidx.at("s.imp.K");
@@ -225,14 +232,17 @@ void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int*
     x = imp;
   }
   const int upc[3] = {C[2], C[1], C[0]};
-  int Hu = m;
+  int Hu = my, Wu = mx;
   for (int k = 0; k < 3; ++k) {
     const bool s1 = (k == 0 && skip);
-    if (!s1) Hu *= 2;
+    if (!s1) {
+      Hu *= 2;
+      Wu *= 2;
+    }
     const std::string p = "s.up" + std::to_string(k + 1);
-    const int a = pl->add_tensor(B, Hu, Hu, upc[k]);
-    const int b = pl->add_tensor(B, Hu, Hu, upc[k]);
-    const int o = pl->add_tensor(B, Hu, Hu, upc[k]);
+    const int a = pl->add_tensor(B, Hu, Wu, upc[k]);
+    const int b = pl->add_tensor(B, Hu, Wu, upc[k]);
+    const int o = pl->add_tensor(B, Hu, Wu, upc[k]);
     pl->layers.push_back(conv_layer(c, p + ".convT.w", p + ".bn0", s1 ? HELM_CONV_T1 : HELM_CONV_T2, x, a, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv1.w", p + ".bn1", HELM_CONV_S1, a, b, -1, -1));
     pl->layers.push_back(conv_layer(c, p + ".conv2.w", p + ".bn2", HELM_CONV_S1, b, o, g[2 - k], -1));
@@ -257,7 +267,7 @@ __global__ void k_fold_bn(const float* __restrict__ params, const float* __restr
   }
 }
 
-int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
+int cnn_derive(helm_cnn* c, int my, int mx, cudaStream_t st) {
   if (!c->params_dev) {
     set_error("cnn: parameters not set (helm_cnn_set_params)");
     return HELM_ESTATE;
@@ -314,12 +324,16 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
     HELM_CUDA(cudaStreamSynchronize(st));  // dmeta is scratch reused below
     for (auto& kv : c->ghat) cudaFree(kv.second);
     c->ghat.clear();
+    for (auto& kv : c->ghat_rect) cudaFree(kv.second);
+    c->ghat_rect.clear();
     c->dirty = false;
   }
-  if (m > 0 && !c->desc.explicit_unet && !c->ghat.count(m)) {
+  const bool sq = my == mx;
+  if (my > 0 && mx > 0 && !c->desc.explicit_unet &&
+      (sq ? !c->ghat.count(my) : !c->ghat_rect.count(std::make_pair(my, mx)))) {
     const ParamInfo& K = c->params[c->pidx.at("s.imp.K")];
     const int nk = K.shape[1];
-    const size_t need = greens_scratch_elems(m, nk);
+    const size_t need = greens_scratch_elems(my, mx, nk);
     if (need > c->gscratch_elems) {
       cudaFree(c->gscratch);
       c->gscratch = nullptr;
@@ -332,18 +346,25 @@ int cnn_derive(helm_cnn* c, int m, cudaStream_t st) {
       c->gscratch_elems = need;
     }
     float2* g = nullptr;
-    if (cudaMalloc(&g, static_cast<size_t>(nk) * 4 * m * m * sizeof(float2)) != cudaSuccess) {
+    if (cudaMalloc(&g, static_cast<size_t>(nk) * 4 * my * mx * sizeof(float2)) != cudaSuccess) {
       set_error("cnn: out of memory for G_hat");
       return HELM_ENOMEM;
     }
-    int rc = launch_greens(c->params_dev + K.offset, nk, m, 1e-5f, c->desc.literal_green, c->gscratch, g, st);
+    int rc = launch_greens(c->params_dev + K.offset, nk, my, mx, 1e-5f, c->desc.literal_green, c->gscratch, g, st);
     if (rc) {
       cudaFree(g);
       return rc;
     }
-    c->ghat[m] = g;
+    if (sq)
+      c->ghat[my] = g;
+    else
+      c->ghat_rect[std::make_pair(my, mx)] = g;
   }
   return HELM_OK;
+}
+
+const float2* ghat_of(const helm_cnn* c, int my, int mx) {
+  return my == mx ? c->ghat.at(my) : c->ghat_rect.at(std::make_pair(my, mx));
 }
 
 size_t wpk_offset(const helm_cnn* c, int param) {
@@ -402,8 +423,8 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
                      c->params_dev + c->params[L.wparam].offset, fold, fold + C, L.act,
                      static_cast<__nv_bfloat16*>(ptr[L.out]), nullptr, st);
     } else {
-      rc = launch_implicit_bf16(static_cast<const __nv_bfloat16*>(ptr[L.in]), in.B, in.H, in.C, c->ghat.at(pl.m),
-                                static_cast<__nv_bfloat16*>(ptr[L.out]), st);
+      rc = launch_implicit_bf16(static_cast<const __nv_bfloat16*>(ptr[L.in]), in.B, in.H, in.W, in.C,
+                                ghat_of(c, pl.my, pl.mx), static_cast<__nv_bfloat16*>(ptr[L.out]), st);
     }
     if (rc) return rc;
   }
@@ -411,10 +432,10 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
 }
 
 // workspace of one network forward at batch B: activation arena + norms
-size_t cnn_forward_bytes(const helm_cnn* c, int I, int B) {
+size_t cnn_forward_bytes(const helm_cnn* c, int H, int W, int B) {
   Plan pl;
   int x0, u3, e[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, e, 1, true);
+  build_solver_plan(c, H, W, B, skip_for(c, H, W), &pl, &x0, &u3, e, 1, true);
   return pl.arena + static_cast<size_t>(B) * 256 * sizeof(double) + 2 * 256 * B * sizeof(float) + 4096;
 }
 
@@ -425,11 +446,11 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
     set_error("cnn: encodings not computed for this problem (call helm_cnn_set_problem)");
     return HELM_ESTATE;
   }
-  const int I = p->nx;
+  const int H = p->ny, W = p->nx;
   Plan pl;
   int x0, u3, enc[3];
-  build_solver_plan(c, I, B, skip_for(c, I), &pl, &x0, &u3, enc, 1, true);
-  int rc = cnn_derive(c, pl.m, st);
+  build_solver_plan(c, H, W, B, skip_for(c, H, W), &pl, &x0, &u3, enc, 1, true);
+  int rc = cnn_derive(c, pl.my, pl.mx, st);
   if (rc) return rc;
   char* arena = cv.take<char>(pl.arena);
   double* part = cv.take<double>(static_cast<size_t>(B) * 256);
@@ -443,33 +464,34 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
   for (size_t i = 0; i < pl.t.size(); ++i) ptr[i] = arena + pl.t[i].off;
   for (int k = 0; k < 3; ++k)
     ptr[enc[k]] = static_cast<char*>(c->enc_arena) + c->enc_plan.t[c->enc_out[k]].off;
-  if ((rc = launch_prep(r, I, B, part, s, inv, static_cast<__nv_bfloat16*>(ptr[x0]), st))) return rc;
+  if ((rc = launch_prep(r, H, W, B, part, s, inv, static_cast<__nv_bfloat16*>(ptr[x0]), st))) return rc;
   if ((rc = run_layers_infer(c, pl, ptr, st))) return rc;
   const ParamInfo& pw = c->params[c->pidx.at("s.proj.w")];
   const ParamInfo& pb = c->params[c->pidx.at("s.proj.b")];
-  return launch_proj(static_cast<const __nv_bfloat16*>(ptr[u3]), B, I / 2, pl.t[u3].C, c->params_dev + pw.offset,
+  return launch_proj(static_cast<const __nv_bfloat16*>(ptr[u3]), B, H / 2, W / 2, pl.t[u3].C, c->params_dev + pw.offset,
                      c->params_dev + pb.offset, s, e, st);
 }
 
 int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
-  const int I = p->nx;
-  if (p->nx != p->ny || I % 16) {
-    set_error("cnn: the network needs a square grid divisible by 16 (got %d x %d)", p->nx, p->ny);
+  const int H = p->ny, W = p->nx;
+  if (H % 16 || W % 16) {
+    set_error("cnn: the network needs grid sides divisible by 16 (got %d x %d)", p->nx, p->ny);
     return HELM_ESHAPE;
   }
   int rc = cnn_derive(c, 0, st);
   if (rc) return rc;
-  if (c->enc_I != I || !c->enc_arena) {
-    build_encoder_plan(c, I, &c->enc_plan, c->enc_out, &c->kf, 1);
+  if (c->enc_H != H || c->enc_W != W || !c->enc_arena) {
+    build_encoder_plan(c, H, W, &c->enc_plan, c->enc_out, &c->kf, 1);
     cudaFree(c->enc_arena);
     c->enc_arena = nullptr;
     if (cudaMalloc(&c->enc_arena, c->enc_plan.arena) != cudaSuccess) {
       c->enc_arena = nullptr;
-      c->enc_I = 0;
+      c->enc_H = c->enc_W = 0;
       set_error("cnn: out of memory for the encodings");
       return HELM_ENOMEM;
     }
-    c->enc_I = I;
+    c->enc_H = H;
+    c->enc_W = W;
   }
   std::vector<void*> ptr(c->enc_plan.t.size());
   for (size_t i = 0; i < ptr.size(); ++i) ptr[i] = static_cast<char*>(c->enc_arena) + c->enc_plan.t[i].off;
@@ -483,7 +505,8 @@ int run_encoder(helm_cnn* c, const helm_problem* p, cudaStream_t st) {
 
 size_t cnn_workspace_bytes(const helm_problem* p, const helm_cnn* cnn, int batch) {
   // forward + e, r' and the compacted input / output of the network
-  return cnn_forward_bytes(cnn, p->nx, batch) + 4 * static_cast<size_t>(batch) * p->npts(0) * sizeof(float2) + 2048;
+  return cnn_forward_bytes(cnn, p->ny, p->nx, batch) + 4 * static_cast<size_t>(batch) * p->npts(0) * sizeof(float2) +
+         2048;
 }
 
 // out[b] = in[sel[b]] (gather, b < nsel) or out[sel[b]] = in[b] (scatter); n points each
@@ -615,6 +638,7 @@ int helm_cnn_destroy(helm_cnn* c) {
   cudaFree(c->gscratch);
   cudaFree(c->enc_arena);
   for (auto& kv : c->ghat) cudaFree(kv.second);
+  for (auto& kv : c->ghat_rect) cudaFree(kv.second);
   delete c;
   return HELM_OK;
 }
@@ -733,6 +757,24 @@ int helm_cnn_get_ghat(helm_cnn* c, int m, void* out_dev, void* stream) {
   if (rc) return rc;
   const int nk = c->params[c->pidx.at("s.imp.K")].shape[1];
   HELM_CUDA(cudaMemcpyAsync(out_dev, c->ghat.at(m), static_cast<size_t>(nk) * 4 * m * m * sizeof(float2),
+                            cudaMemcpyDeviceToDevice, st));
+  return HELM_OK;
+}
+
+int helm_cnn_get_ghat_rect(helm_cnn* c, int my, int mx, void* out_dev, void* stream) {
+  if (!c || my <= 0 || mx <= 0 || !out_dev) {
+    helm::set_error("helm_cnn_get_ghat_rect: invalid argument");
+    return HELM_EINVAL;
+  }
+  if (c->desc.explicit_unet) {
+    helm::set_error("helm_cnn_get_ghat_rect: the explicit U-Net has no implicit layer");
+    return HELM_ESTATE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = helm::cnn_derive(c, my, mx, st);
+  if (rc) return rc;
+  const int nk = c->params[c->pidx.at("s.imp.K")].shape[1];
+  HELM_CUDA(cudaMemcpyAsync(out_dev, helm::ghat_of(c, my, mx), static_cast<size_t>(nk) * 4 * my * mx * sizeof(float2),
                             cudaMemcpyDeviceToDevice, st));
   return HELM_OK;
 }

@@ -44,10 +44,11 @@ struct Layer {
   int wp_dw = -1, bn_dw = -1, wp_proj = -1, bn_proj = -1;
 };
 
-// A plan for one (I, B, skip) configuration: tensors and layers of either the encoder
-// (batch 1) or the solver (batch B).
+// A plan for one (H x W grid, B, skip) configuration: tensors and layers of either the
+// encoder (batch 1) or the solver (batch B).  The coarsest map is my x mx; m = my on the
+// paper's square grids (training plans are square).
 struct Plan {
-  int I = 0, B = 0, skip = 0, m = 0;
+  int H = 0, W = 0, B = 0, skip = 0, m = 0, my = 0, mx = 0;
   std::vector<TensorDesc> t;
   std::vector<Layer> layers;
   size_t arena = 0;  // bytes of all activation tensors
@@ -77,14 +78,15 @@ struct helm_cnn {
                                       // (expansion BF16, projection FP16 bits)
   size_t wfold_elems = 0;
   std::map<int, size_t> wfold_off;    // parameter index -> element offset in wfold
-  std::map<int, float2*> ghat;        // owned: Green's function per coarsest size m
+  std::map<int, float2*> ghat;        // owned: Green's function per coarsest size m (square maps)
+  std::map<std::pair<int, int>, float2*> ghat_rect;   // owned: per (m_y, m_x) of rectangular maps
   float2* gscratch = nullptr;
   size_t gscratch_elems = 0;
   bool dirty = true;                  // params/running changed since the last derive()
   // encodings cached for one problem
   const helm_problem* enc_prob = nullptr;
   unsigned long long enc_pversion = 0;  // enc_prob->version the encodings were computed for
-  int enc_I = 0;
+  int enc_H = 0, enc_W = 0;
   unsigned long long enc_version = 0, param_version = 0;
   void* enc_arena = nullptr;
   size_t enc_arena_bytes = 0;
@@ -98,13 +100,18 @@ namespace helm {
 
 // parameter and BN lookup
 inline int P(const helm_cnn* c, const std::string& n) { return c->pidx.at(n); }
-void build_encoder_plan(const helm_cnn* c, int I, Plan* pl, int* outs, int* kf, int Bk);
+void build_encoder_plan(const helm_cnn* c, int H, int W, Plan* pl, int* outs, int* kf, int Bk);
 // fuse_ib: each inverted bottleneck as one L_IB layer (inference); otherwise expansion,
 // depthwise and projection as separate layers with their activations (training)
-void build_solver_plan(const helm_cnn* c, int I, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
+void build_solver_plan(const helm_cnn* c, int H, int W, int B, int skip, Plan* pl, int* x0, int* u3, int enc_ids[3],
                        int Bk, bool fuse_ib = false);
-int cnn_derive(helm_cnn* c, int m, cudaStream_t st);  // pack weights, fold BN, build G_hat(m)
-int skip_for(const helm_cnn* c, int I);
+// pack weights, fold BN, build G_hat of the my x mx coarsest map (none when my = 0)
+int cnn_derive(helm_cnn* c, int my, int mx, cudaStream_t st);
+inline int cnn_derive(helm_cnn* c, int m, cudaStream_t st) { return cnn_derive(c, m, m, st); }
+// G_hat of the my x mx coarsest map (derived by cnn_derive)
+const float2* ghat_of(const helm_cnn* c, int my, int mx);
+// skip the solver's last downsampling: the shorter side below the threshold
+int skip_for(const helm_cnn* c, int H, int W);
 size_t packed_elems(const helm_cnn* c, const ParamInfo& pi);
 size_t wpk_offset(const helm_cnn* c, int param);
 size_t cnn_train_bytes(const helm_cnn* c, int I, int B, int nprob);

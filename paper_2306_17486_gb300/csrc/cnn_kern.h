@@ -8,18 +8,19 @@
 namespace helm {
 
 int launch_kfeat(const float* kappa, const float* gamma, long n, __nv_bfloat16* out, cudaStream_t st);
-int launch_prep(const float2* r, int N, int B, double* part, float* s, float* inv, __nv_bfloat16* x0,
+// grids are Ny x Nx (rows x columns); the paper's grids are square
+int launch_prep(const float2* r, int Ny, int Nx, int B, double* part, float* s, float* inv, __nv_bfloat16* x0,
                 cudaStream_t st);
 int launch_dw(const __nv_bfloat16* x, int B, int H, int W, int C, const float* w, const float* scale,
               const float* shift, int act, __nv_bfloat16* y, float* yraw, cudaStream_t st);
 size_t implicit_smem(int m);
-int launch_implicit_bf16(const __nv_bfloat16* x, int B, int m, int C, const float2* ghat, __nv_bfloat16* y,
-                         cudaStream_t st);
+int launch_implicit_bf16(const __nv_bfloat16* x, int B, int my, int mx, int C, const float2* ghat,
+                         __nv_bfloat16* y, cudaStream_t st);
 int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* ghat, float* gx, cudaStream_t st);
-size_t greens_scratch_elems(int m, int nk);
-int launch_greens(const float* Kpar, int nk, int m, float eps, int literal, float2* scratch, float2* ghat,
+size_t greens_scratch_elems(int my, int mx, int nk);
+int launch_greens(const float* Kpar, int nk, int my, int mx, float eps, int literal, float2* scratch, float2* ghat,
                   cudaStream_t st);
-int launch_proj(const __nv_bfloat16* u, int B, int Nc, int C, const float* w, const float* bias, const float* s,
+int launch_proj(const __nv_bfloat16* u, int B, int Ncy, int Ncx, int C, const float* w, const float* bias, const float* s,
                 float2* e, cudaStream_t st);
 
 }  // namespace helm

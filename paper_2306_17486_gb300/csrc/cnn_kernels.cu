@@ -58,24 +58,24 @@ __global__ void k_norm_final(const double* __restrict__ part, int nblk, int B, l
 
 // x0[b][J][K][0..1] = (Re, Im) of I_h^H (r_b / s_b): full weighting, zero padding
 // (s_b the RMS of r_b)
-__global__ void k_prep_restrict(const float2* __restrict__ r, int N, int B, const float* __restrict__ inv,
+__global__ void k_prep_restrict(const float2* __restrict__ r, int Ny, int Nx, int B, const float* __restrict__ inv,
                                 bf16* __restrict__ x0) {
-  const int Nc = N / 2;
-  const long total = static_cast<long>(B) * Nc * Nc;
+  const int Ncy = Ny / 2, Ncx = Nx / 2;
+  const long total = static_cast<long>(B) * Ncy * Ncx;
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
-    const int b = static_cast<int>(i / (static_cast<long>(Nc) * Nc));
-    const int J = static_cast<int>((i / Nc) % Nc), K = static_cast<int>(i % Nc);
-    const float2* rb = r + static_cast<long>(b) * N * N;
+    const int b = static_cast<int>(i / (static_cast<long>(Ncy) * Ncx));
+    const int J = static_cast<int>((i / Ncx) % Ncy), K = static_cast<int>(i % Ncx);
+    const float2* rb = r + static_cast<long>(b) * Ny * Nx;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = -1; a <= 1; ++a)
 #pragma unroll
       for (int c = -1; c <= 1; ++c) {
         const int y = 2 * J + a, x = 2 * K + c;
-        if (y < 0 || y >= N || x < 0 || x >= N) continue;
+        if (y < 0 || y >= Ny || x < 0 || x >= Nx) continue;
         const float w = (a == 0 ? 2.f : 1.f) * (c == 0 ? 2.f : 1.f) * (1.f / 16.f);
-        const float2 v = rb[static_cast<long>(y) * N + x];
+        const float2 v = rb[static_cast<long>(y) * Nx + x];
         acc.x += w * v.x;
         acc.y += w * v.y;
       }
@@ -253,20 +253,21 @@ __device__ __forceinline__ float2 load_pair<bf16>(const bf16* p, long idx, int C
   return make_float2(__bfloat162float(p[idx * C + k]), __bfloat162float(p[idx * C + k + C / 2]));
 }
 
-// The 2m x 2m transforms of the implicit layer run as mixed-radix FFTs (Stockham
-// autosort: every stage reads one buffer and writes the other in natural order, so no
-// digit reversal is needed), batched over the lines of a phase and spread over the
-// CTA's threads:
-//   rows     R[r][.]  = FFT(pad(X[r][.]))                     r < m
-//   columns  R[.][u]  = IFFT(G_hat[.][u] . FFT(pad(R[.][u])))  kept for rows < m
-//   rows     Y[r][c]  = IFFT(R[r][.])[c] / (2m)^2             r, c < m
-// Each phase runs in chunks of cw lines, so that shared memory holds R (m x 2m) and two
-// cw x 2m line buffers.
-// n = 2m is factored into radices 8, 9, 4, 2, 3, 5 (8 and 9 as in-register 4 x 2 and
+// The 2m_y x 2m_x transforms of the implicit layer (an m_y x m_x coarsest map; m_y = m_x
+// = m on the paper's square grids) run as mixed-radix FFTs (Stockham autosort: every
+// stage reads one buffer and writes the other in natural order, so no digit reversal is
+// needed), batched over the lines of a phase and spread over the CTA's threads:
+//   rows     R[r][.]  = FFT(pad(X[r][.]))                     r < m_y, length 2m_x
+//   columns  R[.][u]  = IFFT(G_hat[.][u] . FFT(pad(R[.][u])))  length 2m_y, kept for r < m_y
+//   rows     Y[r][c]  = IFFT(R[r][.])[c] / (4 m_y m_x)         r < m_y, c < m_x
+// Each phase runs in chunks of cw lines, so that shared memory holds R (m_y x 2m_x) and
+// two line buffers of cw lines of the longer length.
+// Each length is factored into radices 8, 9, 4, 2, 3, 5 (8 and 9 as in-register 4 x 2 and
 // 3 x 3 decompositions) and any other prime up to FFT_PMAX (direct DFT of that size);
-// twiddles come from one table W[e] = exp(-2 pi i e / n).
+// twiddles come from one table per length, W[e] = exp(-2 pi i e / n) (one shared table
+// when the two lengths are equal).
 constexpr int FFT_MAXF = 16;
-constexpr int FFT_PMAX = 16;
+constexpr int FFT_PMAX = 17;
 struct FftPlan {
   int nf;              // stages
   int f[FFT_MAXF];     // radix of each stage
@@ -399,69 +400,78 @@ __device__ float2* fft_lines(float2* a, float2* b, int L, int n, const FftPlan& 
   return a;
 }
 
-// Eq. 14 for one (sample b, complex channel k): y = crop(IFFT(G_hat_k . FFT(pad(x)))),
-// or with conj_g the adjoint (conj(G_hat_k)); accumulate adds into y (FP32 output only).
+// Eq. 14 for one (sample b, complex channel k) of an m_y x m_x map:
+// y = crop(IFFT(G_hat_k . FFT(pad(x)))), or with conj_g the adjoint (conj(G_hat_k));
+// accumulate adds into y (FP32 output only).  G_hat_k is [2m_y][2m_x].
 // Registers are capped so that three CTAs share an SM at m = 36 (62.8 KB each).
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(256, 3) k_implicit(const TIn* __restrict__ x, int m, int C, const float2* __restrict__ ghat,
-                                                  int conj_g, TOut* __restrict__ y, int accumulate, int cw,
-                                                  FftPlan plan) {
+__global__ void __launch_bounds__(256, 3) k_implicit(const TIn* __restrict__ x, int my, int mx, int C,
+                                                  const float2* __restrict__ ghat, int conj_g, TOut* __restrict__ y,
+                                                  int accumulate, int cw, FftPlan planx, FftPlan plany) {
   const int b = blockIdx.y, k = blockIdx.x;
-  const int n = 2 * m;
+  const int nx = 2 * mx, ny = 2 * my;      // row and column lengths of the padded map
+  const int nl = max(nx, ny);
   extern __shared__ float2 ism[];
-  float2* Wt = ism;               // n
-  float2* R = Wt + n;             // m x n: the rows' spectra, later the columns' results
-  float2* P0 = R + m * n;         // cw x n ping-pong buffers of the line transforms
-  float2* P1 = P0 + cw * n;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  float2* Wx = ism;                          // nx
+  float2* Wy = ny == nx ? Wx : Wx + nx;      // ny (the same table on a square map)
+  float2* R = Wx + nx + (ny == nx ? 0 : ny); // m_y x nx: the rows' spectra, later the columns' results
+  float2* P0 = R + my * nx;                  // cw x nl ping-pong buffers of the line transforms
+  float2* P1 = P0 + cw * nl;
+  for (int e = threadIdx.x; e < nx; e += blockDim.x) {
     float s, c;
-    sincospif(-2.f * e / n, &s, &c);
-    Wt[e] = make_float2(c, s);
+    sincospif(-2.f * e / nx, &s, &c);
+    Wx[e] = make_float2(c, s);
   }
-  const long base = static_cast<long>(b) * m * m;
-  for (int r0 = 0; r0 < m; r0 += cw) {
-    const int w = min(cw, m - r0);
-    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
-      const int r = i / n, c = i - r * n;
-      P0[i] = c < m ? load_pair<TIn>(x, base + (r0 + r) * m + c, C, k) : make_float2(0.f, 0.f);
+  if (ny != nx)
+    for (int e = threadIdx.x; e < ny; e += blockDim.x) {
+      float s, c;
+      sincospif(-2.f * e / ny, &s, &c);
+      Wy[e] = make_float2(c, s);
+    }
+  const long base = static_cast<long>(b) * my * mx;
+  for (int r0 = 0; r0 < my; r0 += cw) {
+    const int w = min(cw, my - r0);
+    for (int i = threadIdx.x; i < w * nx; i += blockDim.x) {
+      const int r = i / nx, c = i - r * nx;
+      P0[i] = c < mx ? load_pair<TIn>(x, base + (r0 + r) * mx + c, C, k) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const float2* rs = fft_lines(P0, P1, w, n, plan, Wt, false);
-    for (int i = threadIdx.x; i < w * n; i += blockDim.x) R[r0 * n + i] = rs[i];
+    const float2* rs = fft_lines(P0, P1, w, nx, planx, Wx, false);
+    for (int i = threadIdx.x; i < w * nx; i += blockDim.x) R[r0 * nx + i] = rs[i];
     __syncthreads();
   }
-  const float2* G = ghat + static_cast<long>(k) * n * n;
-  for (int u0 = 0; u0 < n; u0 += cw) {
-    const int w = min(cw, n - u0);
-    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
-      const int l = i / n, v = i - l * n;
-      P0[i] = v < m ? R[v * n + u0 + l] : make_float2(0.f, 0.f);
+  const float2* G = ghat + static_cast<long>(k) * ny * nx;
+  for (int u0 = 0; u0 < nx; u0 += cw) {
+    const int w = min(cw, nx - u0);
+    for (int i = threadIdx.x; i < w * ny; i += blockDim.x) {
+      const int l = i / ny, v = i - l * ny;
+      P0[i] = v < my ? R[v * nx + u0 + l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* fs = fft_lines(P0, P1, w, n, plan, Wt, false);
-    for (int i = threadIdx.x; i < w * n; i += blockDim.x) {
-      const int l = i / n, v = i - l * n;
-      float2 g = G[static_cast<long>(v) * n + u0 + l];
+    float2* fs = fft_lines(P0, P1, w, ny, plany, Wy, false);
+    for (int i = threadIdx.x; i < w * ny; i += blockDim.x) {
+      const int l = i / ny, v = i - l * ny;
+      float2 g = G[static_cast<long>(v) * nx + u0 + l];
       if (conj_g) g.y = -g.y;
       fs[i] = cmul(fs[i], g);
     }
     __syncthreads();
-    const float2* is = fft_lines(fs, fs == P0 ? P1 : P0, w, n, plan, Wt, true);
-    for (int i = threadIdx.x; i < w * m; i += blockDim.x) {
-      const int l = i / m, v = i - l * m;
-      R[v * n + u0 + l] = is[l * n + v];
+    const float2* is = fft_lines(fs, fs == P0 ? P1 : P0, w, ny, plany, Wy, true);
+    for (int i = threadIdx.x; i < w * my; i += blockDim.x) {
+      const int l = i / my, v = i - l * my;
+      R[v * nx + u0 + l] = is[l * ny + v];
     }
     __syncthreads();
   }
-  const float sc = 1.f / static_cast<float>(n * n);
-  for (int r0 = 0; r0 < m; r0 += cw) {
-    const int w = min(cw, m - r0);
+  const float sc = 1.f / static_cast<float>(nx * ny);
+  for (int r0 = 0; r0 < my; r0 += cw) {
+    const int w = min(cw, my - r0);
     // the chunk's rows of R are consumed here, so they serve as one of the two buffers
-    const float2* ys = fft_lines(R + r0 * n, P0, w, n, plan, Wt, true);
-    for (int i = threadIdx.x; i < w * m; i += blockDim.x) {
-      const int r = i / m, c = i - r * m;
-      const float2 v = cscale(ys[r * n + c], sc);
-      const long idx = (base + (r0 + r) * m + c) * C;
+    const float2* ys = fft_lines(R + r0 * nx, P0, w, nx, planx, Wx, true);
+    for (int i = threadIdx.x; i < w * mx; i += blockDim.x) {
+      const int r = i / mx, c = i - r * mx;
+      const float2 v = cscale(ys[r * nx + c], sc);
+      const long idx = (base + (r0 + r) * mx + c) * C;
       if constexpr (sizeof(TOut) == 2) {
         y[idx + k] = __float2bfloat16_rn(v.x);
         y[idx + k + C / 2] = __float2bfloat16_rn(v.y);
@@ -499,52 +509,59 @@ static bool fft_plan(int n, FftPlan* p) {
   return true;
 }
 
-// shared memory of k_implicit with column chunks of width cw
-static size_t implicit_chunk_smem(int m, int cw) {
-  const size_t n = 2 * m;
-  return (n + m * n + 2 * static_cast<size_t>(cw) * n) * sizeof(float2);
+// shared memory of k_implicit on an m_y x m_x map with chunks of cw lines
+static size_t implicit_chunk_smem(int my, int mx, int cw) {
+  const size_t nx = 2 * mx, ny = 2 * my, nl = std::max(nx, ny);
+  return (nx + (ny == nx ? 0 : ny) + my * nx + 2 * static_cast<size_t>(cw) * nl) * sizeof(float2);
 }
-// the widest chunk (in equal parts of the 2m columns) whose CTA fits 76 KB (three CTAs
+// the widest chunk (in equal parts of the 2m_x columns) whose CTA fits 76 KB (three CTAs
 // per SM), else 200 KB; 0 if none does
-static int implicit_chunk(int m) {
-  const int n = 2 * m;
+static int implicit_chunk(int my, int mx) {
+  const int n = 2 * mx;
   for (size_t cap : {size_t(76) * 1024, size_t(200) * 1024})
     for (int parts = 1; parts <= n; ++parts) {
       const int cw = (n + parts - 1) / parts;
-      if (implicit_chunk_smem(m, cw) <= cap) return cw;
+      if (implicit_chunk_smem(my, mx, cw) <= cap) return cw;
     }
   return 0;
 }
 
 // ---- Green's function of a learned 3x3 kernel (Eq. 15), one CTA per channel ---------
-// Kpar: [2][nk][3][3] (real, imaginary parts).  n6 = 6m periodic grid, source at the
-// centre: G at offsets d (|d| <= m) is (1/n6^2) sum_{u,v} H(u,v) e^{+2 pi i (u dy + v dx)/n6}
-// with H = conj(Kh)/(|Kh|^2 + eps) (or Kh/(Kh^2 + eps)); crop to offsets -m..m-1 with
-// offset 0 at index 0, then G_hat = DFT_{2m}.  scratch: n6*n6 (H) + n6*2m (T) complex.
-__global__ void k_greens(const float* __restrict__ Kpar, int nk, int m, float eps, int literal,
+// Kpar: [2][nk][3][3] (real, imaginary parts).  An m_y x m_x coarsest map takes the
+// 6m_y x 6m_x periodic grid, source at the centre: G at offsets (dy, dx) (|dy| <= m_y,
+// |dx| <= m_x) is (1/(36 m_y m_x)) sum_{u,v} H(u,v) e^{+2 pi i (u dy / 6m_y + v dx / 6m_x)}
+// with H = conj(Kh)/(|Kh|^2 + eps) (or Kh/(Kh^2 + eps)); crop to offsets -m..m-1 per axis
+// with offset 0 at index 0, then G_hat = DFT_{2m_y x 2m_x}.
+// scratch per channel: 6m_y*6m_x (H) + 6m_y*2m_x (T) + 2m_y*2m_x (Gc) complex.
+__global__ void k_greens(const float* __restrict__ Kpar, int nk, int my, int mx, float eps, int literal,
                          float2* __restrict__ scratch, float2* __restrict__ ghat) {
   const int k = blockIdx.x;
-  const int n6 = 6 * m, n = 2 * m;
-  float2* H = scratch + static_cast<long>(k) * (n6 * n6 + n6 * n + n * n);
-  float2* T = H + n6 * n6;
-  float2* Gc = T + n6 * n;
+  const int n6y = 6 * my, n6x = 6 * mx, ny = 2 * my, nx = 2 * mx;
+  // the two axes' phases over one common period (the grid's point count when the axes
+  // differ; one axis' length on a square grid)
+  const bool sq = n6y == n6x;
+  const int per = sq ? n6x : n6y * n6x;
+  const int fy = sq ? 1 : n6x, fx = sq ? 1 : n6y;
+  float2* H = scratch + static_cast<long>(k) * (n6y * n6x + n6y * nx + ny * nx);
+  float2* T = H + n6y * n6x;
+  float2* Gc = T + n6y * nx;
   float Kr[9], Ki[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     Kr[t] = Kpar[k * 9 + t];
     Ki[t] = Kpar[(nk + k) * 9 + t];
   }
-  for (int i = threadIdx.x; i < n6 * n6; i += blockDim.x) {
-    const int u = i / n6, v = i % n6;
+  for (int i = threadIdx.x; i < n6y * n6x; i += blockDim.x) {
+    const int u = i / n6x, v = i % n6x;
     float2 kh = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = -1; a <= 1; ++a)
 #pragma unroll
       for (int c = -1; c <= 1; ++c) {
         float s, co;
-        // exp(-2 pi i (u a + v c) / n6), argument reduced mod n6 exactly in integers
-        const int e = ((u * a + v * c) % n6 + n6) % n6;
-        sincospif(-2.f * e / n6, &s, &co);
+        // exp(-2 pi i (u a / n6y + v c / n6x)), argument reduced mod the period in integers
+        const int e = ((u * a * fy + v * c * fx) % per + per) % per;
+        sincospif(-2.f * e / per, &s, &co);
         const int t = (a + 1) * 3 + (c + 1);
         kh = cadd(kh, cmul(make_float2(Kr[t], Ki[t]), make_float2(co, s)));
       }
@@ -561,67 +578,68 @@ __global__ void k_greens(const float* __restrict__ Kpar, int nk, int m, float ep
     H[i] = h;
   }
   __syncthreads();
-  // T[u][j] = sum_v H[u][v] e^{+2 pi i v d_j / n6}, d_j = j for j < m else j - 2m
-  for (int i = threadIdx.x; i < n6 * n; i += blockDim.x) {
-    const int u = i / n, j = i % n;
-    const int d = j < m ? j : j - n;
+  // T[u][j] = sum_v H[u][v] e^{+2 pi i v d_j / n6x}, d_j = j for j < m_x else j - 2m_x
+  for (int i = threadIdx.x; i < n6y * nx; i += blockDim.x) {
+    const int u = i / nx, j = i % nx;
+    const int d = j < mx ? j : j - nx;
     float2 acc = make_float2(0.f, 0.f);
-    for (int v = 0; v < n6; ++v) {
+    for (int v = 0; v < n6x; ++v) {
       float s, co;
-      const int e = ((v * d) % n6 + n6) % n6;
-      sincospif(2.f * e / n6, &s, &co);
-      acc = cadd(acc, cmul(H[u * n6 + v], make_float2(co, s)));
+      const int e = ((v * d) % n6x + n6x) % n6x;
+      sincospif(2.f * e / n6x, &s, &co);
+      acc = cadd(acc, cmul(H[u * n6x + v], make_float2(co, s)));
     }
     T[i] = acc;
   }
   __syncthreads();
-  const float sc = 1.f / (static_cast<float>(n6) * n6);
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int ii = i / n, j = i % n;
-    const int d = ii < m ? ii : ii - n;
+  // Gc[i][j] = sum_u T[u][j] e^{+2 pi i u d_i / n6y} / (n6y n6x), d_i = i for i < m_y else i - 2m_y
+  const float sc = 1.f / (static_cast<float>(n6y) * n6x);
+  for (int i = threadIdx.x; i < ny * nx; i += blockDim.x) {
+    const int ii = i / nx, j = i % nx;
+    const int d = ii < my ? ii : ii - ny;
     float2 acc = make_float2(0.f, 0.f);
-    for (int u = 0; u < n6; ++u) {
+    for (int u = 0; u < n6y; ++u) {
       float s, co;
-      const int e = ((u * d) % n6 + n6) % n6;
-      sincospif(2.f * e / n6, &s, &co);
-      acc = cadd(acc, cmul(T[u * n + j], make_float2(co, s)));
+      const int e = ((u * d) % n6y + n6y) % n6y;
+      sincospif(2.f * e / n6y, &s, &co);
+      acc = cadd(acc, cmul(T[u * nx + j], make_float2(co, s)));
     }
     Gc[i] = cscale(acc, sc);
   }
   __syncthreads();
-  // G_hat = DFT_{2m}(Gc): rows then columns, reusing T as scratch
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int r = i / n, q = i % n;
+  // G_hat = DFT(Gc): along rows (length 2m_x), then along columns (length 2m_y), T as scratch
+  for (int i = threadIdx.x; i < ny * nx; i += blockDim.x) {
+    const int r = i / nx, q = i % nx;
     float2 acc = make_float2(0.f, 0.f);
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < nx; ++j) {
       float s, co;
-      sincospif(-2.f * ((q * j) % n) / n, &s, &co);
-      acc = cadd(acc, cmul(Gc[r * n + j], make_float2(co, s)));
+      sincospif(-2.f * ((q * j) % nx) / nx, &s, &co);
+      acc = cadd(acc, cmul(Gc[r * nx + j], make_float2(co, s)));
     }
     T[i] = acc;
   }
   __syncthreads();
-  float2* out = ghat + static_cast<long>(k) * n * n;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int p = i / n, q = i % n;
+  float2* out = ghat + static_cast<long>(k) * ny * nx;
+  for (int i = threadIdx.x; i < ny * nx; i += blockDim.x) {
+    const int p = i / nx, q = i % nx;
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < n; ++r) {
+    for (int r = 0; r < ny; ++r) {
       float s, co;
-      sincospif(-2.f * ((p * r) % n) / n, &s, &co);
-      acc = cadd(acc, cmul(T[r * n + q], make_float2(co, s)));
+      sincospif(-2.f * ((p * r) % ny) / ny, &s, &co);
+      acc = cadd(acc, cmul(T[r * nx + q], make_float2(co, s)));
     }
     out[i] = acc;
   }
 }
 
 // ---- projection 1x1 (C -> 2, + bias) at I/2, bilinear prolongation to I, times s ----
-// one CTA per (sample b, coarse row J): the 1x1 projections of coarse rows J and J + 1
-// are computed once into shared memory, then the CTA writes fine rows 2J and 2J + 1
-// (bilinear P: even fine index = coarse value, odd = mean of the two neighbours, zero
-// beyond the last coarse row / column)
+// one CTA per (sample b, coarse row J) of the Ncy x Ncx coarse grid: the 1x1 projections
+// of coarse rows J and J + 1 are computed once into shared memory, then the CTA writes
+// fine rows 2J and 2J + 1 (bilinear P: even fine index = coarse value, odd = mean of the
+// two neighbours, zero beyond the last coarse row / column)
 constexpr int PJ_C = 16;
 constexpr int PJ_MAXNC = 2048;
-__global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u, int B, int Nc, int C,
+__global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u, int B, int Ncy, int Ncx, int C,
                                                       const float* __restrict__ w, const float* __restrict__ bias,
                                                       const float* __restrict__ s, float2* __restrict__ e) {
   __shared__ float2 Pk[2][PJ_MAXNC + 1];
@@ -633,11 +651,11 @@ __global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u
     w1[ch] = w[C + ch];
   }
   const float b0 = bias[0], b1 = bias[1];
-  for (int i = threadIdx.x; i < 2 * (Nc + 1); i += blockDim.x) {
-    const int a = i / (Nc + 1), K = i - a * (Nc + 1);
+  for (int i = threadIdx.x; i < 2 * (Ncx + 1); i += blockDim.x) {
+    const int a = i / (Ncx + 1), K = i - a * (Ncx + 1);
     float2 pv = make_float2(0.f, 0.f);
-    if (J + a < Nc && K < Nc) {
-      const uint4* up = reinterpret_cast<const uint4*>(u + ((static_cast<long>(b) * Nc + J + a) * Nc + K) * C);
+    if (J + a < Ncy && K < Ncx) {
+      const uint4* up = reinterpret_cast<const uint4*>(u + ((static_cast<long>(b) * Ncy + J + a) * Ncx + K) * C);
       float p0 = b0, p1 = b1;
 #pragma unroll
       for (int h = 0; h < PJ_C / 8; ++h) {
@@ -655,15 +673,15 @@ __global__ void __launch_bounds__(256) k_proj_prolong(const bf16* __restrict__ u
     Pk[a][K] = pv;
   }
   __syncthreads();
-  const int N = 2 * Nc;
+  const int Ny = 2 * Ncy, Nx = 2 * Ncx;
   const float sc = s[b];
-  for (int i = threadIdx.x; i < 2 * Nc; i += blockDim.x) {
-    const int af = i / Nc, K = i - af * Nc;   // fine row 2J + af, fine columns 2K, 2K + 1
+  for (int i = threadIdx.x; i < 2 * Ncx; i += blockDim.x) {
+    const int af = i / Ncx, K = i - af * Ncx;   // fine row 2J + af, fine columns 2K, 2K + 1
     const float2 r0 = af ? cscale(cadd(Pk[0][K], Pk[1][K]), 0.5f) : Pk[0][K];
     const float2 r1 = af ? cscale(cadd(Pk[0][K + 1], Pk[1][K + 1]), 0.5f) : Pk[0][K + 1];
     const float2 ev = cscale(r0, sc);
     const float2 od = cscale(cscale(cadd(r0, r1), 0.5f), sc);
-    float2* eo = e + (static_cast<long>(b) * N + 2 * J + af) * N + 2 * K;
+    float2* eo = e + (static_cast<long>(b) * Ny + 2 * J + af) * Nx + 2 * K;
     *reinterpret_cast<float4*>(eo) = make_float4(ev.x, ev.y, od.x, od.y);
   }
 }
@@ -677,13 +695,15 @@ int launch_kfeat(const float* kappa, const float* gamma, long n, bf16* out, cuda
   return HELM_OK;
 }
 
-int launch_prep(const float2* r, int N, int B, double* part, float* s, float* inv, bf16* x0, cudaStream_t st) {
-  const long n = static_cast<long>(N) * N;
+int launch_prep(const float2* r, int Ny, int Nx, int B, double* part, float* s, float* inv, bf16* x0,
+                cudaStream_t st) {
+  const long n = static_cast<long>(Ny) * Nx;
   const int nblk = std::max(1, std::min(256, div_up(n, 4096)));
   HELM_LAUNCH("k_norm_partial", st, k_norm_partial<<<dim3(nblk, B), 256, 0, st>>>(r, n, nblk, part));
   HELM_LAUNCH("k_norm_final", st, k_norm_final<<<div_up(B, 64), 64, 0, st>>>(part, nblk, B, n, s, inv));
   HELM_LAUNCH("k_prep_restrict", st,
-              k_prep_restrict<<<grid_for(static_cast<long>(B) * (N / 2) * (N / 2)), 256, 0, st>>>(r, N, B, inv, x0));
+              k_prep_restrict<<<grid_for(static_cast<long>(B) * (Ny / 2) * (Nx / 2)), 256, 0, st>>>(r, Ny, Nx, B, inv,
+                                                                                                    x0));
   HELM_CHECK_LAUNCH("prep");
   return HELM_OK;
 }
@@ -717,69 +737,75 @@ int launch_dw(const bf16* x, int B, int H, int W, int C, const float* w, const f
 
 size_t implicit_smem(int m) { return static_cast<size_t>(2 * m + m * m + m * 2 * m + 4 * m * m) * sizeof(float2); }
 
-// chunk width and FFT plan of an m x m implicit layer, or an error
-static int implicit_setup(int m, int* cw, FftPlan* plan) {
-  *cw = implicit_chunk(m);
-  if (!*cw) {
-    set_error("implicit layer: %dx%d coarsest map exceeds shared memory", m, m);
+// chunk width and FFT plans (rows of length 2m_x, columns of length 2m_y) of an
+// m_y x m_x implicit layer, or an error
+static int implicit_setup(int my, int mx, int* cw, FftPlan* planx, FftPlan* plany) {
+  if (my <= 0 || mx <= 0) {
+    set_error("implicit layer: empty %dx%d coarsest map", my, mx);
     return HELM_ESHAPE;
   }
-  if (!fft_plan(2 * m, plan)) {
-    set_error("implicit layer: 2m = %d has a prime factor above %d", 2 * m, FFT_PMAX);
+  *cw = implicit_chunk(my, mx);
+  if (!*cw) {
+    set_error("implicit layer: %dx%d coarsest map exceeds shared memory", my, mx);
+    return HELM_ESHAPE;
+  }
+  if (!fft_plan(2 * mx, planx) || !fft_plan(2 * my, plany)) {
+    set_error("implicit layer: 2m_x = %d or 2m_y = %d has a prime factor above %d", 2 * mx, 2 * my, FFT_PMAX);
     return HELM_ESHAPE;
   }
   return HELM_OK;
 }
 
-int launch_implicit_bf16(const bf16* x, int B, int m, int C, const float2* ghat, bf16* y, cudaStream_t st) {
+int launch_implicit_bf16(const bf16* x, int B, int my, int mx, int C, const float2* ghat, bf16* y, cudaStream_t st) {
   int cw;
-  FftPlan plan;
-  if (int rc = implicit_setup(m, &cw, &plan)) return rc;
+  FftPlan planx, plany;
+  if (int rc = implicit_setup(my, mx, &cw, &planx, &plany)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<bf16, bf16>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit", st,
-              k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(x, m, C, ghat, 0, y, 0,
-                                                                                             cw, plan));
+              k_implicit<bf16, bf16><<<dim3(C / 2, B), 256, implicit_chunk_smem(my, mx, cw), st>>>(
+                  x, my, mx, C, ghat, 0, y, 0, cw, planx, plany));
   HELM_CHECK_LAUNCH("k_implicit");
   return HELM_OK;
 }
 
 int launch_implicit_adjoint(const float* gy, int B, int m, int C, const float2* ghat, float* gx, cudaStream_t st) {
   int cw;
-  FftPlan plan;
-  if (int rc = implicit_setup(m, &cw, &plan)) return rc;
+  FftPlan planx, plany;
+  if (int rc = implicit_setup(m, m, &cw, &planx, &plany)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = smem_attr_once(k_implicit<float, float>, 200 * 1024, &attr_done)) return rc;
   HELM_LAUNCH("k_implicit_adj", st,
-              k_implicit<float, float><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, cw), st>>>(gy, m, C, ghat, 1, gx, 1,
-                                                                                               cw, plan));
+              k_implicit<float, float><<<dim3(C / 2, B), 256, implicit_chunk_smem(m, m, cw), st>>>(
+                  gy, m, m, C, ghat, 1, gx, 1, cw, planx, plany));
   HELM_CHECK_LAUNCH("k_implicit_adj");
   return HELM_OK;
 }
 
-size_t greens_scratch_elems(int m, int nk) {
-  const long n6 = 6 * m, n = 2 * m;
-  return static_cast<size_t>(nk) * (n6 * n6 + n6 * n + n * n);
+size_t greens_scratch_elems(int my, int mx, int nk) {
+  const long n6y = 6 * my, n6x = 6 * mx, ny = 2 * my, nx = 2 * mx;
+  return static_cast<size_t>(nk) * (n6y * n6x + n6y * nx + ny * nx);
 }
 
-int launch_greens(const float* Kpar, int nk, int m, float eps, int literal, float2* scratch, float2* ghat,
+int launch_greens(const float* Kpar, int nk, int my, int mx, float eps, int literal, float2* scratch, float2* ghat,
                   cudaStream_t st) {
-  HELM_LAUNCH("k_greens", st, k_greens<<<nk, 256, 0, st>>>(Kpar, nk, m, eps, literal, scratch, ghat));
+  HELM_LAUNCH("k_greens", st, k_greens<<<nk, 256, 0, st>>>(Kpar, nk, my, mx, eps, literal, scratch, ghat));
   HELM_CHECK_LAUNCH("k_greens");
   return HELM_OK;
 }
 
-int launch_proj(const bf16* u, int B, int Nc, int C, const float* w, const float* bias, const float* s, float2* e,
-                cudaStream_t st) {
+int launch_proj(const bf16* u, int B, int Ncy, int Ncx, int C, const float* w, const float* bias, const float* s,
+                float2* e, cudaStream_t st) {
   if (C != PJ_C) {
     set_error("projection: kernel built for %d input channels", PJ_C);
     return HELM_EINVAL;
   }
-  if (Nc > PJ_MAXNC || B > 65535) {
-    set_error("projection: coarse size %d or batch %d beyond the kernel's limits (%d, 65535)", Nc, B, PJ_MAXNC);
+  if (Ncx > PJ_MAXNC || Ncy > 65535 || B > 65535) {
+    set_error("projection: coarse grid %d x %d or batch %d beyond the kernel's limits (width %d, 65535 rows and "
+              "samples)", Ncy, Ncx, B, PJ_MAXNC);
     return HELM_ESHAPE;
   }
-  HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<dim3(Nc, B), 256, 0, st>>>(u, B, Nc, C, w, bias, s, e));
+  HELM_LAUNCH("k_proj_prolong", st, k_proj_prolong<<<dim3(Ncy, B), 256, 0, st>>>(u, B, Ncy, Ncx, C, w, bias, s, e));
   HELM_CHECK_LAUNCH("k_proj_prolong");
   return HELM_OK;
 }
@@ -796,6 +822,17 @@ extern "C" int helm_implicit_bf16(const void* x, int batch, int m, int c, const 
     set_error("helm_implicit_bf16: channels must be a multiple of 8 (NHWC groups of 8)");
     return HELM_EINVAL;
   }
-  return launch_implicit_bf16(static_cast<const bf16*>(x), batch, m, c, static_cast<const float2*>(ghat),
+  return launch_implicit_bf16(static_cast<const bf16*>(x), batch, m, m, c, static_cast<const float2*>(ghat),
+                              static_cast<bf16*>(y), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y,
+                                       void* stream) {
+  using namespace helm;
+  if (!x || !ghat || !y || x == y || batch <= 0 || my <= 0 || mx <= 0 || c <= 0 || c % 8) {
+    set_error("helm_implicit_rect_bf16: invalid argument (channels a multiple of 8, distinct x and y)");
+    return HELM_EINVAL;
+  }
+  return launch_implicit_bf16(static_cast<const bf16*>(x), batch, my, mx, c, static_cast<const float2*>(ghat),
                               static_cast<bf16*>(y), static_cast<cudaStream_t>(stream));
 }

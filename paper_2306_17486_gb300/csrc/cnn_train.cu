@@ -909,8 +909,8 @@ static const int kMaxChunks = 2048;   // BN / projection reduction blocks
 static const int kMaxWChunks = 512;   // weight-gradient pixel chunks
 
 static void carve_train(const helm_cnn* c, int I, int B, int nprob, Carve& cv, TrainState* T, bool with_backward) {
-  build_encoder_plan(c, I, &T->enc, T->enc_out, &T->kf, nprob);
-  build_solver_plan(c, I, B, skip_for(c, I), &T->sol, &T->x0, &T->u3, T->enc_ids, nprob);
+  build_encoder_plan(c, I, I, &T->enc, T->enc_out, &T->kf, nprob);
+  build_solver_plan(c, I, I, B, skip_for(c, I, I), &T->sol, &T->x0, &T->u3, T->enc_ids, nprob);
   char* ea = cv.take<char>(T->enc.arena);
   char* sa = cv.take<char>(T->sol.arena);
   T->eptr.resize(T->enc.t.size());
@@ -993,7 +993,7 @@ static int run_layers_train(helm_cnn* c, const Plan& pl, const std::vector<void*
     const TensorDesc& out = pl.t[L.out];
     int rc = HELM_OK;
     if (L.kind == L_IMPL) {
-      rc = launch_implicit_bf16(static_cast<const bf16*>(ptr[L.in]), in.B, in.H, in.C, c->ghat.at(pl.m),
+      rc = launch_implicit_bf16(static_cast<const bf16*>(ptr[L.in]), in.B, in.H, in.W, in.C, c->ghat.at(pl.m),
                                 static_cast<bf16*>(ptr[L.out]), st);
       if (rc) return rc;
       continue;
@@ -1071,11 +1071,11 @@ int cnn_forward_train(helm_cnn* c, const helm_problem* const* probs, int nprob, 
                            static_cast<bf16*>(T.eptr[T.kf]) + static_cast<size_t>(k) * p->npts(0) * 2, st)))
       return rc;
   if ((rc = run_layers_train(c, T.enc, T.eptr, T.eraw, T.emean, T.eistd, T.part, st))) return rc;
-  if ((rc = launch_prep(r, I, B, T.part, T.s, T.inv, static_cast<bf16*>(T.sptr[T.x0]), st))) return rc;
+  if ((rc = launch_prep(r, I, I, B, T.part, T.s, T.inv, static_cast<bf16*>(T.sptr[T.x0]), st))) return rc;
   if ((rc = run_layers_train(c, T.sol, T.sptr, T.sraw, T.smean, T.sistd, T.part, st))) return rc;
   const ParamInfo& pw = c->params[c->pidx.at("s.proj.w")];
   const ParamInfo& pb = c->params[c->pidx.at("s.proj.b")];
-  rc = launch_proj(static_cast<const bf16*>(T.sptr[T.u3]), B, I / 2, T.sol.t[T.u3].C, c->params_dev + pw.offset,
+  rc = launch_proj(static_cast<const bf16*>(T.sptr[T.u3]), B, I / 2, I / 2, T.sol.t[T.u3].C, c->params_dev + pw.offset,
                    c->params_dev + pb.offset, T.s, e, st);
   if (rc) return rc;
   HELM_CUDA(cudaMemcpyAsync(T.esave, e, static_cast<size_t>(B) * I * I * sizeof(float2), cudaMemcpyDeviceToDevice,

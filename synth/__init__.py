@@ -92,6 +92,26 @@ def salt_kappa(n: int, abl: int, seed: int = 0) -> np.ndarray:
     return _embed_abl(_to_range(f), abl)
 
 
+def rect_kappa(h: int, w: int, abl: int, seed: int = 0, kind: str = "grf") -> np.ndarray:
+    """A rectangular model: an h x w interior (rows x columns) cut from the top-left of a
+    square model of side max(h, w) ('grf', 'layered_grf' or 'salt' above), edge-replicated
+    into the absorbing layer.  Returns float64 [h + 2 abl][w + 2 abl]."""
+    n = max(h, w)
+    make = {"grf": lambda: grf_kappa(n, 0, seed=seed), "layered_grf": lambda: layered_grf_kappa(n, 0, seed=seed),
+            "salt": lambda: salt_kappa(n, 0, seed=seed)}[kind]
+    return _embed_abl(make()[:h, :w], abl)
+
+
+def rect_point_sources(h: int, w: int, abl: int, count: int, seed: int) -> np.ndarray:
+    """`count` unit point sources at seeded positions inside the interior of an
+    (h + 2 abl) x (w + 2 abl) grid, one per right-hand side: complex128 [count][H][W]."""
+    rng = np.random.default_rng(seed)
+    b = np.zeros((count, h + 2 * abl, w + 2 * abl), dtype=np.complex128)
+    for i in range(count):
+        b[i, abl + rng.integers(0, h), abl + rng.integers(0, w)] = 1.0
+    return b
+
+
 def centre_source(N: int) -> np.ndarray:
     """h^2-scaled right-hand side of a unit point source at the grid centre:
     h^2 g = 1 at node (N//2, N//2).  complex128 [N][N]."""

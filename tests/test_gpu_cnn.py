@@ -105,6 +105,99 @@ def test_network_forward_matches_oracle(helm, I, skip_threshold, B, explicit):
     assert np.linalg.norm(e3 - 3 * e) <= 2.0 ** -8 * np.linalg.norm(3 * e)
 
 
+@pytest.mark.parametrize("my,mx", [(4, 6), (6, 4), (5, 7)])
+def test_green_function_rectangular_matches_oracle(helm, my, mx):
+    """Eq. 15 for an m_y x m_x coarsest map (6m_y x 6m_x periodic grid, 2m_y x 2m_x crop;
+    the oracle's rectangular form is pinned by brute-force DFT sums), next to the
+    square table of the same handle."""
+    P, running = _random_net(3)
+    net = helm.Cnn()
+    net.load_dict(P)
+    g = net.ghat((my, mx)).cpu().numpy()
+    ref = ocnn.build_ghat(P, (my, mx))
+    assert g.shape == ref.shape == (P["s.imp.K"].shape[1], 2 * my, 2 * mx)
+    err = np.abs(g - ref).max() / np.abs(ref).max()
+    assert err < 2e-5, err
+    gs = net.ghat(my).cpu().numpy()
+    refs = ocnn.build_ghat(P, my)
+    assert np.abs(gs - refs).max() / np.abs(refs).max() < 2e-5
+
+
+def _rect_kappa(H, W, abl, seed):
+    """A GRF slowness model on an H x W grid (the crop of a square model)."""
+    return synth.grf_kappa(max(H, W) - 2 * abl, abl, 6.0, seed)[:H, :W].astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("H,W,skip_threshold,B", [(64, 96, 512, 2), (96, 64, 512, 1), (128, 192, 64, 2),
+                                                   (80, 112, 512, 1)])
+def test_rectangular_network_forward_matches_oracle(helm, H, W, skip_threshold, B):
+    """The network on an H x W grid (the out-of-distribution shapes of Section 5.1 are
+    rectangles): every layer per axis, the coarsest map m_y x m_x (I/8 per axis with the
+    last downsampling skipped, I/16 without; 80 x 112 takes 2m = 20 and 28, the direct
+    radices 5 and 7), against the oracle on the same BF16 weights, 2-norm as for the
+    square grids."""
+    P, running = _random_net(5)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn(skip_threshold=skip_threshold)
+    net.load_dict(Pq)
+    net.load_running(running)
+    abl = 8
+    kappa = _rect_kappa(H, W, abl, 7)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(np.ascontiguousarray(kappa), dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    r = synth.random_complex((B, H, W), 9).astype(np.complex64).astype(np.complex128)
+    e = net.apply(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    assert e.shape == (B, H, W)
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    on = ocnn.Network(Pq, running, c0=16)
+    ref, _ = on.forward(r, ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64)),
+                        train=False, skip=min(H, W) < skip_threshold)
+    for i in range(B):
+        err = np.linalg.norm(e[i] - ref[i]) / np.linalg.norm(ref[i])
+        print(f"{H}x{W} sample {i}: 2-norm relative error {err:.2e}")
+        assert err < 4e-2, (i, err)
+
+
+def test_rectangular_composed_preconditioner_matches_oracle(helm):
+    """z = e + V(r - A e) (Section 4.1) on a 64 x 96 grid."""
+    H, W, abl, B = 64, 96, 8, 2
+    P, running = _random_net(11)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn()
+    net.load_dict(Pq)
+    net.load_running(running)
+    kappa = _rect_kappa(H, W, abl, 2)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(np.ascontiguousarray(kappa), dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    r = synth.random_complex((B, H, W), 4).astype(np.complex64).astype(np.complex128)
+    z = net.precond(p, torch.tensor(r, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    mg = omg.SLMultigrid(op, 3)
+    on = ocnn.Network(Pq, running, c0=16)
+    kf = ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64))
+    from oracle.training import composed_preconditioner
+    M = composed_preconditioner(op, on, kf, mg)
+    for i in range(B):
+        ref = M(r[i])
+        err = np.linalg.norm(z[i] - ref) / np.linalg.norm(ref)
+        assert err < 4e-2, err
+
+
+def test_rectangular_grid_rejected_by_training(helm):
+    """Training needs a square grid: the rectangular network is an inference path."""
+    net = helm.Cnn()
+    P, running = _random_net(2)
+    net.load_dict(P)
+    kappa = _rect_kappa(64, 96, 8, 3)
+    p = helm.Problem(torch.tensor(np.ascontiguousarray(kappa), dtype=torch.float32, device="cuda"), 8,
+                     ohz.omega_h_for_ppw(kappa.max()), levels=3)
+    r = torch.zeros((2, 64, 96), dtype=torch.complex64, device="cuda")
+    with pytest.raises(RuntimeError, match="square"):
+        net.apply(p, r, train=True)
+
+
 @pytest.mark.parametrize("explicit", [False, True], ids=["implicit", "explicit"])
 def test_composed_preconditioner_matches_oracle(helm, explicit):
     I, abl, B = 64, 8, 2

@@ -239,3 +239,42 @@ def test_trainer_resume_is_bitwise(helm, tmp_path):
     assert torch.equal(tr_a.opt.m, tr_b.opt.m) and torch.equal(tr_a.opt.v, tr_b.opt.v)
     # and the resumed run really trained: the parameters moved from the checkpoint
     assert not np.array_equal(np.load(ckpt)["params"], net_b.params.cpu().numpy())
+
+
+def test_trained_network_on_a_rectangular_grid(helm, tmp_path):
+    """The committed network (trained on squares) on a 192 x 320 grid (a rectangle, as
+    the out-of-distribution models of Section 5.1): FGMRES(10) with the network on every
+    third step converges on every RHS, judged by the oracle's FP64 true residual, and
+    the output survives a save / load (the rectangular G_hat is derived again from the
+    stored kernels)."""
+    from paper_2306_17486_gb300 import train as T
+    H, W, abl, B = 192, 320, 16, 4
+    net = helm.Cnn(skip_threshold=256)
+    T.load_weights(net, WEIGHTS)
+    kap = synth.grf_kappa(W - 2 * abl, abl, 8.0, seed=14)[:H].astype(np.float32).astype(np.float64)
+    oh = 2 * np.pi / 10 / kap.max()
+    p = helm.Problem(torch.tensor(np.ascontiguousarray(kap), dtype=torch.float32, device="cuda"), abl, oh, levels=4)
+    net.set_problem(p)
+    rng = np.random.default_rng(3)
+    b = np.zeros((B, H, W), dtype=np.complex128)
+    for i in range(B):
+        b[i, rng.integers(abl, H - abl), rng.integers(abl, W - abl)] = 1.0
+    bg = torch.tensor(b, dtype=torch.complex64, device="cuda")
+    x, st = helm.fgmres_solve(p, bg, cnn=net, restart=10, rtol=1e-6, maxit=2000, warmup_iters=3, cnn_every=3)
+    _, st_mg = helm.fgmres_solve(p, bg, restart=10, rtol=1e-6, maxit=2000)
+    print(f"192x320: iterations with the network {st['iters'].tolist()}, SL-MG alone {st_mg['iters'].tolist()}")
+    op = ohz.Problem(kap, abl, omega_h=oh)
+    xs = x.cpu().numpy()
+    for i in range(B):
+        assert st["status"][i] == 1, st
+        assert np.linalg.norm(b[i] - op.A(xs[i])) <= 1e-6 * np.linalg.norm(b[i])
+    r = torch.tensor(synth.random_complex((2, H, W), 5), dtype=torch.complex64, device="cuda")
+    e0 = net.apply(p, r)
+    path = str(tmp_path / "net.helmcnn")
+    net.save(path)
+    net2 = helm.Cnn(skip_threshold=256)
+    net2.load(path)
+    net2.set_problem(p)
+    assert torch.equal(net2.apply(p, r), e0)
+    assert torch.equal(net2.ghat((H // 8, W // 8)), net.ghat((H // 8, W // 8)))
+    assert helm.device_errors() == 0

@@ -4,7 +4,8 @@ at the benchmark's shape.
 
 * The fused inverted bottleneck (Section 4.4, MobileNetV2 block; helm_ib_bf16) at
   C = 16, 32, 64 on grids with ragged tiles (the kernel tiles 8 x 16 outputs).
-* The implicit layer (Section 4.2, Eq. 14; helm_implicit_bf16) at m = 8, 36 and 72.
+* The implicit layer (Section 4.2, Eq. 14; helm_implicit_bf16) at m = 8, 36 and 72, and
+  on m_y x m_x maps (helm_implicit_rect_bf16).
 * The network forward at I = 576 with the layer plan the benchmark runs (coarsest
   level I/16, batch 8, the persistent kernels wrapping over their segments), 2-norm.
 
@@ -169,6 +170,53 @@ def test_implicit_layer_matches_oracle_per_element(helm, m, B):
     y = np.transpose(yg.double().cpu().numpy(), (0, 3, 1, 2))
     worst = float((np.abs(y - y_ref) / bound).max())
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("my,mx,B", [(8, 12, 2), (12, 8, 1), (5, 7, 2), (36, 68, 1)])
+def test_rectangular_implicit_layer_matches_oracle_per_element(helm, my, mx, B):
+    """Eq. 14 on an m_y x m_x map (helm_implicit_rect_bf16): rows of length 2m_x, columns
+    of length 2m_y, with the FFT radices 8, 4, 2, 3 and the direct prime radices 5, 7 and
+    17 (2m_x = 136 of the 576 x 1088 grid).  The bound is the square one with the two
+    lengths: two dense DFT stages of each, 2 (2m_x + 2m_y) eps32 of max|G_hat| sum|x|."""
+    C = 64
+    nk = C // 2
+    rng = np.random.default_rng(100 * my + mx)
+    K = np.stack([np.broadcast_to(oimp.laplacian_plus_i().real, (nk, 3, 3)),
+                  np.broadcast_to(oimp.laplacian_plus_i().imag, (nk, 3, 3))]).copy()
+    K += 0.2 * rng.standard_normal(K.shape)
+    ghat = np.stack([oimp.greens_hat(K[0, k] + 1j * K[1, k], (my, mx)) for k in range(nk)])
+    ghat = ghat.astype(np.complex64).astype(np.complex128)
+    x = _bf(rng.standard_normal((B, C, my, mx)))
+    tp = ocnn.Tape({}, record=False)
+    y_ref = ocnn.implicit_layer(tp, ocnn.Var(x), "unused", ghat).a
+    xs = x[:, :nk] + 1j * x[:, nk:]
+    mag = np.abs(xs).sum(axis=(2, 3))
+    gmax = np.abs(ghat).max(axis=(1, 2))
+    tail = 2 * (2 * mx + 2 * my) * 2.0 ** -24 * gmax[None, :] * mag
+    tail = np.concatenate([tail, tail], axis=1)[:, :, None, None]
+    bound = UB * np.abs(y_ref) + tail
+    xg = torch.tensor(np.transpose(x, (0, 2, 3, 1)), dtype=torch.float32, device="cuda").to(torch.bfloat16)
+    xg = xg.contiguous()
+    yg = torch.empty_like(xg)
+    gg = torch.tensor(ghat, dtype=torch.complex64, device="cuda")
+    helm._lib.check(helm.lib().helm_implicit_rect_bf16(helm._ptr(xg), B, my, mx, C, helm._ptr(gg), helm._ptr(yg),
+                                                       helm._stream()), "helm_implicit_rect_bf16")
+    y = np.transpose(yg.double().cpu().numpy(), (0, 3, 1, 2))
+    worst = float((np.abs(y - y_ref) / bound).max())
+    print(f"implicit {my}x{mx}: worst error/bound {worst:.3f}")
+    assert worst <= 1.0, worst
+
+
+def test_implicit_layer_rejects_a_prime_factor_above_the_radix_limit(helm):
+    """2m_x = 38 = 2 x 19: no FFT plan, HELM_ESHAPE before any launch."""
+    C, B, my, mx = 16, 1, 4, 19
+    xg = torch.zeros((B, my, mx, C), dtype=torch.bfloat16, device="cuda")
+    yg = torch.empty_like(xg)
+    gg = torch.zeros((C // 2, 2 * my, 2 * mx), dtype=torch.complex64, device="cuda")
+    rc = helm.lib().helm_implicit_rect_bf16(helm._ptr(xg), B, my, mx, C, helm._ptr(gg), helm._ptr(yg),
+                                            helm._stream())
+    assert rc == -2                      # HELM_ESHAPE
+    assert "prime factor" in helm.lib().helm_last_error_string().decode()
 
 
 def test_network_forward_at_the_benchmark_shape(helm):
