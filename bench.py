@@ -14,10 +14,11 @@ nodes, 5-level V-cycle), 2 slowness models x 16 point sources, each arm timed on
 nodes, 8 right-hand sides each) served by captured solver plans, with and without the
 network; and `ood_shapes`: the trained network against SL-MG alone on the rectangular
 out-of-distribution shapes of Section 5.1 (512 x 1024 and 352 x 800 interiors, 8 point
-sources each).
+sources each); and `workload_2176`: the 2048^2 interior (2176^2 nodes, 6-level V-cycle),
+one model x 8 point sources, the network against SL-MG alone.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--skip-1152]
-        [--skip-serving] [--skip-ood]
+        [--skip-serving] [--skip-ood] [--skip-2176]
         (N > 1: launched by torchrun, one replica per GPU, independent models per rank)
 """
 from __future__ import annotations
@@ -253,6 +254,49 @@ OOD_SHAPES = ((512, 1024, "layered_grf"), (352, 800, "salt"))
 OOD_ABL, OOD_LEVELS, OOD_RHS = 32, 4, 8
 
 
+# The 2048^2 interior (+ 64-cell layer = 2176^2 nodes, 6-level V-cycle, coarsest 68^2):
+# one GRF model x 8 point sources; the network's coarsest map (136^2) takes the
+# three-pass implicit layer
+N2K_INT, N2K_ABL, N2K_LEVELS, N2K_RHS, N2K_MAXIT = 2048, 64, 6, 8, 8000
+
+
+def run_2176(helm, net, dev, rank: int):
+    """ms per RHS and iterations to 1e-6 on the 2176^2 grid: the network on every
+    CNN_EVERY-th step against SL-MG alone, one timed pass per arm after an untimed
+    warm-up solve, inputs resident in HBM."""
+    import torch
+    import synth
+    N = N2K_INT + 2 * N2K_ABL
+    kap = synth.grf_kappa(N2K_INT, N2K_ABL, 8.0, seed=60 + rank)
+    oh = 2.0 * np.pi / (10.0 * float(kap.max()))
+    p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device=dev), N2K_ABL, oh, levels=N2K_LEVELS)
+    b = torch.tensor(synth.random_point_sources(N, N2K_ABL, N2K_RHS, seed=6000 + rank), dtype=torch.complex64,
+                     device=dev)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device=dev)
+    p.workspace(N2K_RHS, RESTART, net)
+    net.set_problem(p)
+    out = {"workload": "helmholtz-2176sq-1kappa-x8rhs-fgmres10", "grid": N, "interior": N2K_INT, "abl": N2K_ABL,
+           "mg_levels": N2K_LEVELS, "rhs": N2K_RHS, "maxit": N2K_MAXIT}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, cnn in (("value", True), ("mg_only", False)):
+        helm.fgmres_solve(p, b, x, cnn=net if cnn else None, restart=RESTART, rtol=RTOL, maxit=30, warmup_iters=3,
+                          cnn_every=CNN_EVERY)
+        x.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        _, st = helm.fgmres_solve(p, b, x, cnn=net if cnn else None, restart=RESTART, rtol=RTOL, maxit=N2K_MAXIT,
+                                  warmup_iters=3, cnn_every=CNN_EVERY)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_rhs": round(e0.elapsed_time(e1) / N2K_RHS, 3),
+                     "iterations_mean": round(float(st["iters"].mean()), 1),
+                     "converged_frac": float(np.mean(st["status"] == 1)),
+                     "max_true_rel_res": float(st["rel_res_true"].max())}
+    out["speedup_vs_mg_only"] = round(out["mg_only"]["ms_per_rhs"] / out["value"]["ms_per_rhs"], 3)
+    del p
+    return out
+
+
 def run_ood(helm, net, dev, rank: int):
     """ms per RHS and iterations to 1e-6 on the rectangular out-of-distribution shapes:
     the trained network (on every CNN_EVERY-th step) against SL-MG alone; one timed pass
@@ -456,6 +500,8 @@ def run_gpu(args, rank: int, world: int):
         out["serving"] = run_serving()
     if not args.skip_ood:
         out["ood_shapes"] = run_ood(helm, net, dev, rank)
+    if not args.skip_2176:
+        out["workload_2176"] = run_2176(helm, net, dev, rank)
     out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
     out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
     if rank == 0:
@@ -717,6 +763,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--skip-1152", action="store_true", help="leave out the 1152^2 (1024^2 interior) workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the mixed-size serving run")
+    ap.add_argument("--skip-2176", action="store_true", help="leave out the 2176^2 (2048^2 interior) workload")
     ap.add_argument("--skip-ood", action="store_true",
                     help="leave out the rectangular out-of-distribution shapes (512 x 1024, 352 x 800)")
     args = ap.parse_args()

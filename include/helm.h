@@ -300,6 +300,21 @@ int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat,
 int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y,
                             void* stream);
 
+/*
+ * The same layer in three passes through a global intermediate, for maps whose
+ * m_y x 2m_x intermediate exceeds a CTA's shared memory (m about 112 and above: the
+ * coarsest maps of grids from about 1792^2 up): the row transforms into the workspace,
+ * the column transforms with the product by ghat in place, then the inverse row
+ * transforms into y.  Arguments as helm_implicit_rect_bf16, plus a device workspace of
+ * helm_implicit_3pass_workspace_size bytes (batch * c/2 * my * 2mx complex64;
+ * HELM_EWORKSPACE if smaller).  The network switches to this form by itself when the
+ * one-CTA form does not fit (its workspace includes the intermediate).  HELM_ESHAPE when
+ * 2m_x or 2m_y exceeds 2048 or has a prime factor above 17.
+ */
+int helm_implicit_3pass_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y, void* ws,
+                             size_t ws_bytes, void* stream);
+int helm_implicit_3pass_workspace_size(int batch, int my, int mx, int c, size_t* bytes);
+
 /* Launch-shape tuning table (process-wide, read at launch time; captured solver plans
  * keep the shapes they were captured with).  A knob's value for a layer of height
  * `height` run on `batch` images overrides the kernel family's launch heuristic.
@@ -312,10 +327,15 @@ int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, con
  *                        allows, up to 32)
  *   HELM_TUNE_IB_SH      output rows per work unit of the 16/32-channel inverted
  *                        bottleneck (a multiple of 4; the heuristic balances the units
- *                        over the SMs)                                                */
+ *                        over the SMs)
+ *   HELM_TUNE_IMPLICIT_3PASS  1: the network's implicit layer on maps of m_y rows runs
+ *                        in three passes (helm_implicit_3pass_bf16) even where the
+ *                        one-CTA form fits (the heuristic takes three passes only
+ *                        where it does not)                                            */
 #define HELM_TUNE_CONV_ROWS 0
 #define HELM_TUNE_IB_SH 1
-#define HELM_TUNE_KNOBS 2
+#define HELM_TUNE_IMPLICIT_3PASS 2
+#define HELM_TUNE_KNOBS 3
 int helm_tune_set(int knob, int height, int batch, int value);
 int helm_tune_get(int knob, int height, int batch, int* value);
 int helm_tune_clear(void);

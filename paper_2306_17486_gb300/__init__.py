@@ -263,7 +263,7 @@ class SolverPlan:
             pass
 
 
-TUNE_KNOBS = {"conv_rows": 0, "ib_sh": 1}
+TUNE_KNOBS = {"conv_rows": 0, "ib_sh": 1, "implicit_3pass": 2}
 
 
 def tune_set(knob: str, height: int, batch: int, value: int):
@@ -281,6 +281,26 @@ def tune_get(knob: str, height: int, batch: int) -> int:
 
 def tune_clear():
     check(lib().helm_tune_clear(), "helm_tune_clear")
+
+
+def profile(fn) -> list:
+    """Run fn() under the library's profiler (helm_profile_*: CUDA events around every
+    launch on its own stream) and return [(kernel name, launches, total ms)], largest
+    total first."""
+    check(lib().helm_profile_begin(), "helm_profile_begin")
+    nk = C.c_int()
+    try:
+        fn()
+        torch.cuda.synchronize()
+    finally:
+        check(lib().helm_profile_end(C.byref(nk)), "helm_profile_end")
+    rows = []
+    for i in range(nk.value):
+        nm, cnt, tot = C.c_char_p(), C.c_long(), C.c_double()
+        check(lib().helm_profile_read(i, C.byref(nm), C.byref(cnt), C.byref(tot)), "helm_profile_read")
+        rows.append((nm.value.decode(), cnt.value, tot.value))
+    rows.sort(key=lambda t: -t[2])
+    return rows
 
 
 def device_errors() -> int:

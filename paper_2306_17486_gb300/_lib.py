@@ -74,6 +74,8 @@ PROTOS = {
     "helm_ib_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     "helm_implicit_bf16": (i32, [vp, i32, i32, i32, vp, vp, vp]),
     "helm_implicit_rect_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+    "helm_implicit_3pass_bf16": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
+    "helm_implicit_3pass_workspace_size": (i32, [i32, i32, i32, i32, C.POINTER(sz)]),
     "helm_cnn_create": (i32, [C.POINTER(CnnDesc), C.POINTER(vp)]),
     "helm_cnn_destroy": (i32, [vp]),
     "helm_cnn_num_params": (i32, [vp, C.POINTER(sz)]),

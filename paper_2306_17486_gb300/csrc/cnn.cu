@@ -373,8 +373,10 @@ size_t wpk_offset(const helm_cnn* c, int param) {
   return off;
 }
 
-// Execute the layers of a plan in inference mode; `ptr[t]` = base of tensor t.
-static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*>& ptr, cudaStream_t st) {
+// Execute the layers of a plan in inference mode; `ptr[t]` = base of tensor t; iscr: the
+// implicit layer's three-pass intermediate (null for the encoder)
+static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*>& ptr, cudaStream_t st,
+                            float2* iscr = nullptr) {
   for (const Layer& L : pl.layers) {
     const TensorDesc& in = pl.t[L.in];
     const TensorDesc& out = pl.t[L.out];
@@ -424,7 +426,7 @@ static int run_layers_infer(helm_cnn* c, const Plan& pl, const std::vector<void*
                      static_cast<__nv_bfloat16*>(ptr[L.out]), nullptr, st);
     } else {
       rc = launch_implicit_bf16(static_cast<const __nv_bfloat16*>(ptr[L.in]), in.B, in.H, in.W, in.C,
-                                ghat_of(c, pl.my, pl.mx), static_cast<__nv_bfloat16*>(ptr[L.out]), st);
+                                ghat_of(c, pl.my, pl.mx), static_cast<__nv_bfloat16*>(ptr[L.out]), st, iscr);
     }
     if (rc) return rc;
   }
@@ -436,7 +438,8 @@ size_t cnn_forward_bytes(const helm_cnn* c, int H, int W, int B) {
   Plan pl;
   int x0, u3, e[3];
   build_solver_plan(c, H, W, B, skip_for(c, H, W), &pl, &x0, &u3, e, 1, true);
-  return pl.arena + static_cast<size_t>(B) * 256 * sizeof(double) + 2 * 256 * B * sizeof(float) + 4096;
+  return pl.arena + static_cast<size_t>(B) * 256 * sizeof(double) + 2 * 256 * B * sizeof(float) +
+         implicit_3pass_bytes(B, pl.my, pl.mx, 4 * c->desc.c0) + 4096;
 }
 
 // e = s Net(r / s), s = RMS(r), in inference mode, scratch from `cv`
@@ -456,6 +459,7 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
   double* part = cv.take<double>(static_cast<size_t>(B) * 256);
   float* s = cv.take<float>(B);
   float* inv = cv.take<float>(B);
+  float2* iscr = cv.take<float2>(implicit_3pass_bytes(B, pl.my, pl.mx, 4 * c->desc.c0) / sizeof(float2));
   if (cv.overflow) {
     set_error("cnn: workspace too small");
     return HELM_EWORKSPACE;
@@ -465,7 +469,7 @@ int cnn_forward_infer(helm_cnn* c, const helm_problem* p, const float2* r, float
   for (int k = 0; k < 3; ++k)
     ptr[enc[k]] = static_cast<char*>(c->enc_arena) + c->enc_plan.t[c->enc_out[k]].off;
   if ((rc = launch_prep(r, H, W, B, part, s, inv, static_cast<__nv_bfloat16*>(ptr[x0]), st))) return rc;
-  if ((rc = run_layers_infer(c, pl, ptr, st))) return rc;
+  if ((rc = run_layers_infer(c, pl, ptr, st, iscr))) return rc;
   const ParamInfo& pw = c->params[c->pidx.at("s.proj.w")];
   const ParamInfo& pb = c->params[c->pidx.at("s.proj.b")];
   return launch_proj(static_cast<const __nv_bfloat16*>(ptr[u3]), B, H / 2, W / 2, pl.t[u3].C, c->params_dev + pw.offset,

@@ -489,6 +489,93 @@ __global__ void __launch_bounds__(256, 3) k_implicit(const TIn* __restrict__ x, 
   }
 }
 
+// The same layer in three passes through a global intermediate Rg [B][C/2][m_y][2m_x]
+// (complex), for maps whose m_y x 2m_x intermediate exceeds a CTA's shared memory.
+// blockIdx = (complex channel k, sample b, chunk of cw lines):
+//   pass 0  rows r0..r0+cw of the zero-padded input: FFT (length 2m_x) -> Rg
+//   pass 1  columns u0..u0+cw of Rg: FFT (length 2m_y, rows >= m_y zero), times G_hat,
+//           inverse FFT, rows < m_y back into Rg
+//   pass 2  rows r0..r0+cw of Rg: inverse FFT, scale 1/(4 m_y m_x), crop to m_x -> y
+// Shared memory: the pass's twiddle table (n) and two cw x n line buffers.
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(256) k_implicit_pass(const TIn* __restrict__ x, int my, int mx, int C,
+                                                       const float2* __restrict__ ghat, int conj_g,
+                                                       float2* __restrict__ Rg, TOut* __restrict__ y, int accumulate,
+                                                       int pass, int cw, FftPlan plan) {
+  const int k = blockIdx.x, b = blockIdx.y, nk = C / 2;
+  const int nx = 2 * mx, ny = 2 * my;
+  const int n = pass == 1 ? ny : nx;        // line length of this pass
+  const int lines = pass == 1 ? nx : my;
+  const int l0 = blockIdx.z * cw;
+  if (l0 >= lines) return;
+  const int w = min(cw, lines - l0);
+  extern __shared__ float2 ism[];
+  float2* Wt = ism;
+  float2* P0 = Wt + n;
+  float2* P1 = P0 + cw * n;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    float s, c;
+    sincospif(-2.f * e / n, &s, &c);
+    Wt[e] = make_float2(c, s);
+  }
+  float2* Rb = Rg + (static_cast<long>(b) * nk + k) * my * nx;   // this (sample, channel)'s m_y x 2m_x block
+  if (pass == 0) {
+    const long base = static_cast<long>(b) * my * mx;
+    for (int i = threadIdx.x; i < w * nx; i += blockDim.x) {
+      const int r = i / nx, c = i - r * nx;
+      P0[i] = c < mx ? load_pair<TIn>(x, base + static_cast<long>(l0 + r) * mx + c, C, k) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2* rs = fft_lines(P0, P1, w, nx, plan, Wt, false);
+    for (int i = threadIdx.x; i < w * nx; i += blockDim.x) Rb[static_cast<long>(l0) * nx + i] = rs[i];
+  } else if (pass == 1) {
+    // column l of the chunk is column l0 + l of Rb; consecutive threads take consecutive
+    // columns of one row, so the global reads and writes are contiguous runs of w
+    for (int i = threadIdx.x; i < w * ny; i += blockDim.x) {
+      const int v = i / w, l = i - v * w;
+      P0[l * ny + v] = v < my ? Rb[static_cast<long>(v) * nx + l0 + l] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* fs = fft_lines(P0, P1, w, ny, plan, Wt, false);
+    const float2* G = ghat + static_cast<long>(k) * ny * nx;
+    for (int i = threadIdx.x; i < w * ny; i += blockDim.x) {
+      const int v = i / w, l = i - v * w;
+      float2 g = G[static_cast<long>(v) * nx + l0 + l];
+      if (conj_g) g.y = -g.y;
+      fs[l * ny + v] = cmul(fs[l * ny + v], g);
+    }
+    __syncthreads();
+    const float2* is = fft_lines(fs, fs == P0 ? P1 : P0, w, ny, plan, Wt, true);
+    for (int i = threadIdx.x; i < w * my; i += blockDim.x) {
+      const int v = i / w, l = i - v * w;
+      Rb[static_cast<long>(v) * nx + l0 + l] = is[l * ny + v];
+    }
+  } else {
+    for (int i = threadIdx.x; i < w * nx; i += blockDim.x) P0[i] = Rb[static_cast<long>(l0) * nx + i];
+    __syncthreads();
+    const float2* ys = fft_lines(P0, P1, w, nx, plan, Wt, true);
+    const float sc = 1.f / static_cast<float>(nx * ny);
+    const long base = static_cast<long>(b) * my * mx;
+    for (int i = threadIdx.x; i < w * mx; i += blockDim.x) {
+      const int r = i / mx, c = i - r * mx;
+      const float2 v = cscale(ys[r * nx + c], sc);
+      const long idx = (base + static_cast<long>(l0 + r) * mx + c) * C;
+      if constexpr (sizeof(TOut) == 2) {
+        y[idx + k] = __float2bfloat16_rn(v.x);
+        y[idx + k + C / 2] = __float2bfloat16_rn(v.y);
+      } else {
+        if (accumulate) {
+          y[idx + k] += v.x;
+          y[idx + k + C / 2] += v.y;
+        } else {
+          y[idx + k] = v.x;
+          y[idx + k + C / 2] = v.y;
+        }
+      }
+    }
+  }
+}
+
 // Radices of n (8s first, then 9, 4, 2, 3, 5, other primes); false if a prime factor exceeds
 // FFT_PMAX or there are too many stages.
 static bool fft_plan(int n, FftPlan* p) {
@@ -756,7 +843,50 @@ static int implicit_setup(int my, int mx, int* cw, FftPlan* planx, FftPlan* plan
   return HELM_OK;
 }
 
-int launch_implicit_bf16(const bf16* x, int B, int my, int mx, int C, const float2* ghat, bf16* y, cudaStream_t st) {
+// lines per CTA of a three-pass line length n: the most (up to 16) whose two buffers and
+// twiddles fit 48 KB
+static int pass_chunk(int n) { return std::max(1, std::min(16, (6144 - n) / (2 * n))); }
+
+size_t implicit_3pass_bytes(int B, int my, int mx, int C) {
+  return static_cast<size_t>(B) * (C / 2) * my * (2 * mx) * sizeof(float2);
+}
+
+// the three passes of k_implicit_pass; scratch holds implicit_3pass_bytes
+static int launch_implicit_3pass(const bf16* x, int B, int my, int mx, int C, const float2* ghat, bf16* y,
+                                 float2* scratch, cudaStream_t st) {
+  FftPlan planx, plany;
+  if (!fft_plan(2 * mx, &planx) || !fft_plan(2 * my, &plany)) {
+    set_error("implicit layer: 2m_x = %d or 2m_y = %d has a prime factor above %d", 2 * mx, 2 * my, FFT_PMAX);
+    return HELM_ESHAPE;
+  }
+  const int nx = 2 * mx, ny = 2 * my;
+  if (nx > 2048 || ny > 2048 || B > 65535 || C / 2 > 65535) {
+    set_error("implicit layer: %dx%d map or batch %d beyond the three-pass kernel's limits", my, mx, B);
+    return HELM_ESHAPE;
+  }
+  for (int pass = 0; pass < 3; ++pass) {
+    const int n = pass == 1 ? ny : nx, lines = pass == 1 ? nx : my;
+    const int cw = pass_chunk(n);
+    const size_t smem = static_cast<size_t>(n + 2 * cw * n) * sizeof(float2);
+    const dim3 grid(C / 2, B, div_up(lines, cw));
+    HELM_LAUNCH("k_implicit_pass", st,
+                k_implicit_pass<bf16, bf16><<<grid, 256, smem, st>>>(x, my, mx, C, ghat, 0, scratch, y, 0, pass, cw,
+                                                                      pass == 1 ? plany : planx));
+  }
+  HELM_CHECK_LAUNCH("k_implicit_pass");
+  return HELM_OK;
+}
+
+int launch_implicit_bf16(const bf16* x, int B, int my, int mx, int C, const float2* ghat, bf16* y, cudaStream_t st,
+                         float2* scratch) {
+  if (my <= 0 || mx <= 0) {
+    set_error("implicit layer: empty %dx%d coarsest map", my, mx);
+    return HELM_ESHAPE;
+  }
+  // three passes when the one-CTA form does not fit shared memory, or when the tuning
+  // table asks for them at this height and batch; they need the caller's scratch
+  if (scratch && (!implicit_chunk(my, mx) || tune_get(HELM_TUNE_IMPLICIT_3PASS, my, B) > 0))
+    return launch_implicit_3pass(x, B, my, mx, C, ghat, y, scratch, st);
   int cw;
   FftPlan planx, plany;
   if (int rc = implicit_setup(my, mx, &cw, &planx, &plany)) return rc;
@@ -824,6 +954,31 @@ extern "C" int helm_implicit_bf16(const void* x, int batch, int m, int c, const 
   }
   return launch_implicit_bf16(static_cast<const bf16*>(x), batch, m, m, c, static_cast<const float2*>(ghat),
                               static_cast<bf16*>(y), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int helm_implicit_3pass_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y,
+                                        void* ws, size_t ws_bytes, void* stream) {
+  using namespace helm;
+  if (!x || !ghat || !y || !ws || x == y || batch <= 0 || my <= 0 || mx <= 0 || c <= 0 || c % 8) {
+    set_error("helm_implicit_3pass_bf16: invalid argument (channels a multiple of 8, distinct x and y, a workspace)");
+    return HELM_EINVAL;
+  }
+  if (ws_bytes < implicit_3pass_bytes(batch, my, mx, c)) {
+    set_error("helm_implicit_3pass_bf16: workspace of %zu bytes, %zu needed", ws_bytes,
+              implicit_3pass_bytes(batch, my, mx, c));
+    return HELM_EWORKSPACE;
+  }
+  return launch_implicit_3pass(static_cast<const bf16*>(x), batch, my, mx, c, static_cast<const float2*>(ghat),
+                               static_cast<bf16*>(y), static_cast<float2*>(ws), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int helm_implicit_3pass_workspace_size(int batch, int my, int mx, int c, size_t* bytes) {
+  if (batch <= 0 || my <= 0 || mx <= 0 || c <= 0 || !bytes) {
+    helm::set_error("helm_implicit_3pass_workspace_size: invalid argument");
+    return HELM_EINVAL;
+  }
+  *bytes = helm::implicit_3pass_bytes(batch, my, mx, c);
+  return HELM_OK;
 }
 
 extern "C" int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, const void* ghat, void* y,

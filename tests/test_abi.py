@@ -73,7 +73,7 @@ def test_tuning_table_lookup_order(L):
     assert L.helm_tune_get(1, 576, 64, ctypes.byref(v)) == 0 and v.value == 0         # other knob untouched
     assert L.helm_tune_set(0, 576, 64, 0) == 0                                         # removed: next entry
     assert L.helm_tune_get(0, 576, 64, ctypes.byref(v)) == 0 and v.value == 8
-    assert L.helm_tune_set(2, 576, 64, 4) == -1                                        # no such knob
+    assert L.helm_tune_set(3, 576, 64, 4) == -1                                        # no such knob
     assert L.helm_tune_set(0, 0, 64, 4) == -1                                          # batch without height
     assert L.helm_tune_set(0, -1, 0, 4) == -1
     assert L.helm_tune_clear() == 0

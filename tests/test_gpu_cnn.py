@@ -159,6 +159,47 @@ def test_rectangular_network_forward_matches_oracle(helm, H, W, skip_threshold, 
         assert err < 4e-2, (i, err)
 
 
+@pytest.mark.parametrize("H,W", [(64, 96), (128, 128)])
+def test_network_with_three_pass_implicit_layer_matches_oracle(helm, H, W):
+    """The network with its implicit layer in three passes through the workspace (the
+    form of the grids whose coarsest map exceeds shared memory, forced here through the
+    tuning table at the coarsest height): against the oracle as above, and against the
+    one-CTA form of the same handle."""
+    B = 2
+    P, running = _random_net(5)
+    Pq = {k: (_bf(v) if (k.endswith(".w") and v.ndim in (2, 4) and k != "s.proj.w") else v) for k, v in P.items()}
+    net = helm.Cnn()
+    net.load_dict(Pq)
+    net.load_running(running)
+    abl = 8
+    kappa = _rect_kappa(H, W, abl, 7)
+    oh = ohz.omega_h_for_ppw(kappa.max())
+    p = helm.Problem(torch.tensor(np.ascontiguousarray(kappa), dtype=torch.float32, device="cuda"), abl, oh, levels=3)
+    net.set_problem(p)
+    r = synth.random_complex((B, H, W), 9).astype(np.complex64).astype(np.complex128)
+    rg = torch.tensor(r, dtype=torch.complex64, device="cuda")
+    e1 = net.apply(p, rg).cpu().numpy()
+    my = H // 8
+    helm.tune_set("implicit_3pass", my, 0, 1)
+    out = {}
+    try:
+        names = [n for n, _, _ in helm.profile(lambda: out.setdefault("e", net.apply(p, rg)))]
+    finally:
+        helm.tune_set("implicit_3pass", my, 0, 0)
+    e3 = out["e"].cpu().numpy()
+    assert "k_implicit_pass" in names and "k_implicit" not in names, names
+    op = ohz.Problem(kappa, abl, omega_h=oh)
+    on = ocnn.Network(Pq, running, c0=16)
+    ref, _ = on.forward(r, ocnn.kappa_features(op.kappa, op.gamma.astype(np.float32).astype(np.float64)),
+                        train=False, skip=True)
+    for i in range(B):
+        err = np.linalg.norm(e3[i] - ref[i]) / np.linalg.norm(ref[i])
+        d13 = np.linalg.norm(e3[i] - e1[i]) / np.linalg.norm(e1[i])
+        print(f"{H}x{W} three-pass sample {i}: vs oracle {err:.2e}, vs one-CTA form {d13:.2e}")
+        assert err < 4e-2, (i, err)
+        assert d13 < 1e-3, (i, d13)
+
+
 def test_rectangular_composed_preconditioner_matches_oracle(helm):
     """z = e + V(r - A e) (Section 4.1) on a 64 x 96 grid."""
     H, W, abl, B = 64, 96, 8, 2

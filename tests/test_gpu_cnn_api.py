@@ -278,3 +278,30 @@ def test_trained_network_on_a_rectangular_grid(helm, tmp_path):
     assert torch.equal(net2.apply(p, r), e0)
     assert torch.equal(net2.ghat((H // 8, W // 8)), net.ghat((H // 8, W // 8)))
     assert helm.device_errors() == 0
+
+
+def test_trained_network_on_the_2176sq_grid(helm):
+    """The network on the 2176^2 grid (2048^2 interior + 64-cell layer; Tables 1-3 go up to
+    4096^2): its coarsest map, 136 x 136, exceeds a CTA's shared memory, so the implicit
+    layer takes the three-pass form by itself.  FGMRES(10) with the network on every
+    third step converges on every RHS, judged by the oracle's FP64 true residual."""
+    from paper_2306_17486_gb300 import train as T
+    N, abl, B = 2176, 64, 2
+    net = helm.Cnn(skip_threshold=256)
+    T.load_weights(net, WEIGHTS)
+    kap = synth.grf_kappa(N - 2 * abl, abl, 8.0, seed=30).astype(np.float32).astype(np.float64)
+    oh = 2 * np.pi / 10 / kap.max()
+    p = helm.Problem(torch.tensor(kap, dtype=torch.float32, device="cuda"), abl, oh, levels=6)
+    net.set_problem(p)
+    b = synth.random_point_sources(N, abl, B, seed=7)
+    bg = torch.tensor(b, dtype=torch.complex64, device="cuda")
+    names = [n for n, _, _ in helm.profile(lambda: net.apply(p, bg))]
+    assert "k_implicit_pass" in names and "k_implicit" not in names, names
+    x, st = helm.fgmres_solve(p, bg, cnn=net, restart=10, rtol=1e-6, maxit=4000, warmup_iters=3, cnn_every=3)
+    print(f"2176^2: iterations with the network {st['iters'].tolist()}")
+    op = ohz.Problem(kap, abl, omega_h=oh)
+    xs = x.cpu().numpy()
+    for i in range(B):
+        assert st["status"][i] == 1, st
+        assert np.linalg.norm(b[i] - op.A(xs[i])) <= 1e-6 * np.linalg.norm(b[i])
+    assert helm.device_errors() == 0

@@ -4,8 +4,9 @@ at the benchmark's shape.
 
 * The fused inverted bottleneck (Section 4.4, MobileNetV2 block; helm_ib_bf16) at
   C = 16, 32, 64 on grids with ragged tiles (the kernel tiles 8 x 16 outputs).
-* The implicit layer (Section 4.2, Eq. 14; helm_implicit_bf16) at m = 8, 36 and 72, and
-  on m_y x m_x maps (helm_implicit_rect_bf16).
+* The implicit layer (Section 4.2, Eq. 14; helm_implicit_bf16) at m = 8, 36 and 72, on
+  m_y x m_x maps (helm_implicit_rect_bf16), and in three passes (helm_implicit_3pass_bf16)
+  up to the 136 x 136 map of the 2176^2 grid.
 * The network forward at I = 576 with the layer plan the benchmark runs (coarsest
   level I/16, batch 8, the persistent kernels wrapping over their segments), 2-norm.
 
@@ -30,6 +31,7 @@ then doubled for margin:
   2m eps32 of the magnitude bound max|G_hat| sum|x|, then BF16 rounding:
       |y - y_ref| <= 2^-8 |y_ref| + 4 (2m) 2^-24 max|G_hat| sum|x|.
 """
+import ctypes
 import os
 
 import numpy as np
@@ -205,6 +207,59 @@ def test_rectangular_implicit_layer_matches_oracle_per_element(helm, my, mx, B):
     worst = float((np.abs(y - y_ref) / bound).max())
     print(f"implicit {my}x{mx}: worst error/bound {worst:.3f}")
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("my,mx,B", [(8, 12, 2), (36, 68, 1), (136, 136, 1)])
+def test_three_pass_implicit_layer_matches_oracle_per_element(helm, my, mx, B):
+    """Eq. 14 in three passes through a global intermediate (helm_implicit_3pass_bf16),
+    the form the network takes when the m_y x 2m_x intermediate exceeds shared memory:
+    136 x 136 is the coarsest map of the 2176^2 grid (2048^2 interior), too large for
+    the one-CTA form, which rejects it with HELM_ESHAPE.  The same per-element bound as
+    the one-CTA form, and at 36 x 68 the two forms agree."""
+    C = 64
+    nk = C // 2
+    rng = np.random.default_rng(7 * my + mx)
+    K = np.stack([np.broadcast_to(oimp.laplacian_plus_i().real, (nk, 3, 3)),
+                  np.broadcast_to(oimp.laplacian_plus_i().imag, (nk, 3, 3))]).copy()
+    K += 0.2 * rng.standard_normal(K.shape)
+    ghat = np.stack([oimp.greens_hat(K[0, k] + 1j * K[1, k], (my, mx)) for k in range(nk)])
+    ghat = ghat.astype(np.complex64).astype(np.complex128)
+    x = _bf(rng.standard_normal((B, C, my, mx)))
+    tp = ocnn.Tape({}, record=False)
+    y_ref = ocnn.implicit_layer(tp, ocnn.Var(x), "unused", ghat).a
+    xs = x[:, :nk] + 1j * x[:, nk:]
+    mag = np.abs(xs).sum(axis=(2, 3))
+    gmax = np.abs(ghat).max(axis=(1, 2))
+    tail = 2 * (2 * mx + 2 * my) * 2.0 ** -24 * gmax[None, :] * mag
+    tail = np.concatenate([tail, tail], axis=1)[:, :, None, None]
+    bound = UB * np.abs(y_ref) + tail
+    xg = torch.tensor(np.transpose(x, (0, 2, 3, 1)), dtype=torch.float32, device="cuda").to(torch.bfloat16)
+    xg = xg.contiguous()
+    yg = torch.empty_like(xg)
+    gg = torch.tensor(ghat, dtype=torch.complex64, device="cuda")
+    n = ctypes.c_size_t()
+    L = helm.lib()
+    helm._lib.check(L.helm_implicit_3pass_workspace_size(B, my, mx, C, ctypes.byref(n)), "workspace size")
+    assert n.value == B * nk * my * 2 * mx * 8
+    ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    assert L.helm_implicit_3pass_bf16(helm._ptr(xg), B, my, mx, C, helm._ptr(gg), helm._ptr(yg), helm._ptr(ws),
+                                      n.value - 1, helm._stream()) == -6          # HELM_EWORKSPACE
+    helm._lib.check(L.helm_implicit_3pass_bf16(helm._ptr(xg), B, my, mx, C, helm._ptr(gg), helm._ptr(yg),
+                                               helm._ptr(ws), n.value, helm._stream()), "helm_implicit_3pass_bf16")
+    y = np.transpose(yg.double().cpu().numpy(), (0, 3, 1, 2))
+    worst = float((np.abs(y - y_ref) / bound).max())
+    print(f"three-pass implicit {my}x{mx}: worst error/bound {worst:.3f}")
+    assert worst <= 1.0, worst
+    y1 = torch.empty_like(xg)
+    rc = L.helm_implicit_rect_bf16(helm._ptr(xg), B, my, mx, C, helm._ptr(gg), helm._ptr(y1), helm._stream())
+    if my == 136:
+        assert rc == -2                                                            # HELM_ESHAPE
+        assert "shared memory" in L.helm_last_error_string().decode()
+    else:
+        helm._lib.check(rc, "helm_implicit_rect_bf16")
+        d = (y1.double() - yg.double()).abs().max().item()
+        print(f"one-CTA vs three-pass {my}x{mx}: max difference {d:.3e}")
+        assert d <= 2.0 ** -7 * yg.double().abs().max().item()
 
 
 def test_implicit_layer_rejects_a_prime_factor_above_the_radix_limit(helm):
