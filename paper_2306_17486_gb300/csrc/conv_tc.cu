@@ -50,7 +50,8 @@ struct ConvArgs {
   int add2_div;          // consecutive samples sharing one add2 entry (1: per sample)
   bf16* y;               // bf16 NHWC output or null
   float* yraw;           // fp32 NHWC raw accumulator or null
-  int seg_q;             // virtual output pixels per segment (whole rows for 3x3)
+  int seg_q;             // virtual output pixels per segment (whole rows for 3x3 where
+                         // a row's window fits shared memory)
   int segs_per_img, nsegs;
   int L;                 // window rows per plane (odd)
 };
@@ -77,8 +78,8 @@ struct ConvCfg {
   static_assert(NH % 16 == 0 && NH <= 256, "N per MMA");
 };
 
-// One CTA works through segments (a band of whole output rows of one image, or for 1x1
-// a run of pixels): all warps stage the segment's input window with asynchronous
+// One CTA works through segments (a band of whole output rows of one image; on grids too
+// wide for one row's window, a run of MMA steps within a row; for 1x1 a run of pixels): all warps stage the segment's input window with asynchronous
 // 16-byte copies (zero-filled outside the image); then warp 8 alone issues the MMAs of
 // every step (one or two 128-pixel M-tiles) into one of two TMEM accumulators, and
 // warps 0-7 run the epilogues.  The hand-off is two mbarrier pairs: `full` (MMA
@@ -446,7 +447,17 @@ int launch_t(const ConvArgs& a0, cudaStream_t st) {
     a.seg_q = R * a.Po;
   }
   a.L = window_rows(a.seg_q);
-  const size_t smem = fixed + plane_row * a.L;
+  size_t smem = fixed + plane_row * a.L;
+  if (TAPS != 1 && smem > 227 * 1024) {
+    // one output row's window exceeds shared memory (the widest grids): segments of
+    // whole MMA steps within a row, the most that fit; the window is addressed on the
+    // flattened virtual grid, so a segment may start and end anywhere in a row
+    int k = helm::div_up(a.Po, 128 * Cfg::MT);
+    while (k > 1 && fixed + plane_row * window_rows(k * 128 * Cfg::MT) > 227 * 1024) --k;
+    a.seg_q = k * 128 * Cfg::MT;
+    a.L = window_rows(a.seg_q);
+    smem = fixed + plane_row * a.L;
+  }
   a.segs_per_img = helm::div_up(static_cast<long>(a.Ho) * a.Po, a.seg_q);
   a.nsegs = a.segs_per_img * a.B;
   if (smem > 227 * 1024) {

@@ -48,6 +48,9 @@ CASES = [  # (cin, cout, taps, mode, H, W)
     (16, 96, 1, "s1", 15, 21), (96, 16, 1, "s1", 15, 21), (32, 192, 1, "s1", 9, 13), (192, 32, 1, "s1", 9, 13),
     (64, 384, 1, "s1", 7, 11), (384, 64, 1, "s1", 7, 11), (16, 16, 9, "s1", 144, 144),
     (16, 16, 9, "t2", 5, 11), (32, 32, 9, "t2", 9, 4), (32, 16, 9, "t2", 72, 72), (64, 32, 9, "t2", 36, 36),
+    # rows too wide for one row's window: segments of MMA steps within a row (the first
+    # encoder convolution and the last solver downsampling of the 2176^2 grid)
+    (2, 16, 9, "s2", 6, 2176), (64, 64, 9, "s2", 8, 272),
 ]
 
 
