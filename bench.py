@@ -502,6 +502,13 @@ def run_gpu(args, rank: int, world: int):
         out["ood_shapes"] = run_ood(helm, net, dev, rank)
     if not args.skip_2176:
         out["workload_2176"] = run_2176(helm, net, dev, rank)
+    # the comparison the metric is about stays at the end of the line, after the other
+    # workloads: the headline's iterations, SL-MG alone, the paper's schedule, then the
+    # scalars
+    for k in ("iterations", "mg_only", "paper_schedule"):
+        out[k] = out.pop(k)
+    out["mg_only_ms_per_rhs"] = out["mg_only"]["value"]
+    out["paper_schedule_ms_per_rhs"] = out["paper_schedule"]["value"]
     out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
     out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
     if rank == 0:
