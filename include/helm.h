@@ -286,7 +286,8 @@ int helm_ib_bf16(const void* x, int batch, int h, int w, int c, const float* w_e
  * which is zero-padded to 2m x 2m, transformed, multiplied by ghat[k] (complex64
  * [c/2][2m][2m], the Green's function of Eq. 15 after crop and DFT, as returned by
  * helm_cnn_get_ghat), transformed back and cropped to the top-left m x m block; y has
- * x's layout, distinct from x.  HELM_ESHAPE for m beyond the shared-memory limit.
+ * x's layout, distinct from x.  HELM_ESHAPE for m beyond the shared-memory limit (about
+ * 111; helm_implicit_3pass_bf16 takes larger maps).
  */
 int helm_implicit_bf16(const void* x, int batch, int m, int c, const void* ghat, void* y, void* stream);
 
