@@ -36,7 +36,7 @@ from . import train as T
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "weights", "cnn_grf_multiscale.npz")
-NET_MAX = 1152          # the network's largest grid (whole-row convolution windows, implicit layer smem)
+NET_MAX = 2304          # the network's largest grid (convolution windows within shared memory)
 
 
 LEVELS = {288: 4, 576: 4, 1152: 5, 2304: 6}   # coarsest grids 36^2, 72^2, 72^2, 72^2
