@@ -335,6 +335,23 @@ def run_ood(helm, net, dev, rank: int):
     return out
 
 
+COMPARISON_KEYS = ("iterations", "mg_only", "paper_schedule", "mg_only_ms_per_rhs", "paper_schedule_ms_per_rhs",
+                   "speedup_vs_mg_only", "paper_schedule_speedup_vs_mg_only")
+
+
+def _end_with_comparison(out: dict, mg_value: float, value: float, pp_value: float) -> dict:
+    """Move the comparison the metric is about to the end of the JSON line, after every
+    other workload: the headline's iterations, SL-MG alone and the paper's schedule, then
+    their ms per RHS and the two speedups as scalars (COMPARISON_KEYS, in that order)."""
+    for k in ("iterations", "mg_only", "paper_schedule"):
+        out[k] = out.pop(k)
+    out["mg_only_ms_per_rhs"] = out["mg_only"]["value"]
+    out["paper_schedule_ms_per_rhs"] = out["paper_schedule"]["value"]
+    out["speedup_vs_mg_only"] = round(mg_value / max(value, 1e-12), 3)
+    out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
+    return out
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     import __graft_entry__
@@ -502,15 +519,7 @@ def run_gpu(args, rank: int, world: int):
         out["ood_shapes"] = run_ood(helm, net, dev, rank)
     if not args.skip_2176:
         out["workload_2176"] = run_2176(helm, net, dev, rank)
-    # the comparison the metric is about stays at the end of the line, after the other
-    # workloads: the headline's iterations, SL-MG alone, the paper's schedule, then the
-    # scalars
-    for k in ("iterations", "mg_only", "paper_schedule"):
-        out[k] = out.pop(k)
-    out["mg_only_ms_per_rhs"] = out["mg_only"]["value"]
-    out["paper_schedule_ms_per_rhs"] = out["paper_schedule"]["value"]
-    out["speedup_vs_mg_only"] = round(mg_value / max(value_job, 1e-12), 3)
-    out["paper_schedule_speedup_vs_mg_only"] = round(mg_value / max(pp_value, 1e-12), 3)
+    _end_with_comparison(out, mg_value, value_job, pp_value)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
