@@ -78,3 +78,33 @@ def test_tuning_table_lookup_order(L):
     assert L.helm_tune_set(0, -1, 0, 4) == -1
     assert L.helm_tune_clear() == 0
     assert L.helm_tune_get(0, 576, 8, ctypes.byref(v)) == 0 and v.value == 0
+
+
+def test_implicit_layer_host_checks_without_gpu(L):
+    """The three-pass implicit layer's workspace query (batch x c/2 x m_y x 2m_x complex64)
+    and the argument checks of the implicit-layer entry points, all on the host."""
+    n = ctypes.c_size_t()
+    assert L.helm_implicit_3pass_workspace_size(8, 136, 136, 64, ctypes.byref(n)) == 0
+    assert n.value == 8 * 32 * 136 * 272 * 8
+    assert L.helm_implicit_3pass_workspace_size(2, 36, 68, 64, ctypes.byref(n)) == 0
+    assert n.value == 2 * 32 * 36 * 136 * 8
+    assert L.helm_implicit_3pass_workspace_size(0, 36, 68, 64, ctypes.byref(n)) == -1
+    fake = ctypes.c_void_p(0x1000)
+    other = ctypes.c_void_p(0x2000)
+    # odd or non-multiple-of-8 channel counts, aliasing, a missing workspace: EINVAL
+    assert L.helm_implicit_rect_bf16(fake, 1, 8, 12, 12, fake, other, None) == -1
+    assert L.helm_implicit_rect_bf16(fake, 1, 8, 12, 16, fake, fake, None) == -1
+    assert L.helm_implicit_3pass_bf16(fake, 1, 8, 12, 16, fake, other, None, 1 << 20, None) == -1
+    # a workspace one byte short: EWORKSPACE before any launch
+    assert L.helm_implicit_3pass_bf16(fake, 1, 8, 12, 16, fake, other, fake, 8 * 8 * 24 * 8 - 1, None) == -6
+    assert b"workspace" in L.helm_last_error_string()
+
+
+def test_implicit_three_pass_tuning_knob(L):
+    """Knob 2 (HELM_TUNE_IMPLICIT_3PASS) is accepted and looked up like the others."""
+    v = ctypes.c_int()
+    assert L.helm_tune_clear() == 0
+    assert L.helm_tune_set(2, 8, 0, 1) == 0
+    assert L.helm_tune_get(2, 8, 64, ctypes.byref(v)) == 0 and v.value == 1
+    assert L.helm_tune_get(2, 16, 64, ctypes.byref(v)) == 0 and v.value == 0
+    assert L.helm_tune_clear() == 0
