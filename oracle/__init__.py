@@ -24,7 +24,8 @@ the iteration counts of a trained network, implicit or explicit (the paper's dat
 and weights are not available).  `training.composed_preconditioner` is pinned by the
 special cases its algebra fixes: a zero network output gives the plain V-cycle, the
 exact error is returned unchanged, and z - e is the V-cycle of the remaining residual.
-Parity unpinned as well: the boundary term that Neumann and Sommerfeld problems put on
-the coarse multigrid levels (a reading of how to rediscretise them, checked only for
-its wiring; the fine-level operator and the cycle built from it are pinned).
+The boundary term that Neumann and Sommerfeld problems put on the coarse multigrid
+levels follows a reading (each level carries the same condition on its own grid); each
+level's operator is pinned against the ghost-value definition of the condition on that
+grid and against its closed forms on the constant vector.
 """

@@ -161,3 +161,40 @@ def test_vcycle_and_fgmres_with_the_boundary_condition(bc, abl):
     xs, res = ofg.fgmres(p.A, b, np.zeros_like(b), mg.SLMultigrid(p, 3), 10, 1e-12, 600)
     ref = np.linalg.solve(Adef, b.ravel()).reshape(N, N)
     assert res.converged and np.linalg.norm(xs - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("bc", ["neumann", "sommerfeld"])
+def test_coarse_levels_are_the_same_boundary_value_problem(bc):
+    """Every multigrid level carries the condition of the fine problem on its own grid
+    (spacing 2^l h, kappa_l = sqrt of the restricted kappa^2).  On levels 0-2 the level's
+    operator equals the ghost-value definition of the condition (u_ghost = c_l u_b, c_l
+    from kappa_l and omega h_l) applied to the level's shifted-Laplacian mass; and with
+    constant kappa it meets the closed forms of the condition on the constant vector:
+    the stencil part vanishes for Neumann (S_l 1 = -mass), and each boundary side adds
+    i omega h_l kappa for first-order Sommerfeld."""
+    N, abl, levels = 32, 4, 3
+    rng = np.random.default_rng(11)
+    p = hz.Problem(synth.grf_kappa(N - 2 * abl, abl, 4.0, 9), abl, bc=bc)
+    M = mg.SLMultigrid(p, levels)
+    k2 = p.kappa ** 2
+    for l in range(levels):
+        oh = p.omega_h * 2 ** l
+        if l:
+            k2 = mg.restrict_average(k2)
+        slm = hz.sl_mass(k2, oh)
+        for _ in range(2):
+            u = rng.standard_normal(k2.shape) + 1j * rng.standard_normal(k2.shape)
+            ref = hz.apply_stencil_ghost(slm, u, bc, np.sqrt(k2), oh)
+            assert np.allclose(M.S(l, u), ref, rtol=0, atol=1e-13 * np.abs(ref).max()), l
+    kc = 0.6
+    pc = hz.Problem(np.full((N, N), kc), abl, bc=bc)
+    Mc = mg.SLMultigrid(pc, levels)
+    for l in range(levels):
+        n = N >> l
+        oh = pc.omega_h * 2 ** l
+        slm = hz.sl_mass(np.full((n, n), kc ** 2), oh)
+        one = np.ones((n, n), dtype=np.complex128)
+        sides = (np.arange(n)[:, None] == 0) * 1.0 + (np.arange(n)[:, None] == n - 1) + \
+            (np.arange(n)[None, :] == 0) + (np.arange(n)[None, :] == n - 1)
+        want = -slm + (0.0 if bc == "neumann" else 1j * oh * kc * sides)
+        assert np.allclose(Mc.S(l, one), want, rtol=0, atol=1e-12), l
