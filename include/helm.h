@@ -108,7 +108,8 @@ int helm_problem_create(const float* kappa_dev, int nx, int ny, int abl, double 
                         const helm_mg_opts* opts, void* stream, helm_problem** out);
 int helm_problem_destroy(helm_problem* p);
 
-/* Recompute problem p's setup fields in place for a new slowness model kappa_dev (same
+/* Recompute problem p's setup fields (those of helm_problem_create: Section 3.1 Eq. 1-3,
+ * Section 3.2 Eq. 4 and 8) in place for a new slowness model kappa_dev (same
  * grid, absorbing layer, gamma0 and multigrid options) and frequency omega_h; the
  * problem's device arrays keep their addresses, so work captured against them (a
  * helm_solver_plan) stays valid.  A network's cached encodings of p become stale:
@@ -155,7 +156,8 @@ int helm_slmg_vcycle(const helm_problem* p, const void* r, void* z, int batch, v
                      void* stream);
 
 /*
- * z = V(r) exactly as helm_slmg_vcycle, without a workspace argument: the scratch is a
+ * z = V(r) exactly as helm_slmg_vcycle (Section 3.2, Algorithm 1), without a workspace
+ * argument: the scratch is a
  * fixed device array inside the library of HELM_VCYCLE_STATIC_BYTES (16 MiB), resident
  * on every device the library is loaded on.  The paper has no counterpart: it is for
  * callers that cannot pass or allocate scratch (e.g. a preconditioner callback of an
@@ -224,7 +226,7 @@ int helm_fgmres_solve(const helm_problem* p, const helm_cnn* cnn, const void* b,
 
 /*
  * A captured solver for repeated solves of one batch shape (mixed-size serving: one
- * plan per grid size).  helm_solver_plan_create binds the problem, the network (NULL:
+ * plan per grid size): the FGMRES of helm_fgmres_solve (Section 4.1; Saad 1993).  helm_solver_plan_create binds the problem, the network (NULL:
  * SL V-cycle only), the right-hand-side buffer b (complex64 [batch][ny][nx]), the
  * solution buffer x (complex128, the initial guess is zero), the options and the
  * workspace (helm_workspace_size), runs every kind of restart cycle once, then records
@@ -302,7 +304,8 @@ int helm_implicit_rect_bf16(const void* x, int batch, int my, int mx, int c, con
                             void* stream);
 
 /*
- * The same layer in three passes through a global intermediate, for maps whose
+ * The same layer (Section 4.2, Eq. 14) in three passes through a global intermediate,
+ * for maps whose
  * m_y x 2m_x intermediate exceeds a CTA's shared memory (m about 112 and above: the
  * coarsest maps of grids from about 1792^2 up): the row transforms into the workspace,
  * the column transforms with the product by ghat in place, then the inverse row
@@ -364,7 +367,8 @@ typedef struct {
                          step at the coarsest level (no "s.imp.K" parameter, no G_hat)     */
 } helm_cnn_desc;
 
-/* Create a network (all parameters owned by the caller, see helm_cnn_set_params); the
+/* Create a network (the encoder-solver U-Net of Sections 4.1-4.4 with the sizes of
+ * Section 5.3; all parameters owned by the caller, see helm_cnn_set_params); the
  * handle owns BN running statistics (initialised to mean 0, var 1), packed BF16
  * weights, the Green's functions per coarsest size and the encodings of one problem. */
 int helm_cnn_create(const helm_cnn_desc* desc, helm_cnn** out);
@@ -439,7 +443,8 @@ int helm_cnn_precond_backward(const helm_problem* p, helm_cnn* c, const void* r,
 int helm_mse_loss(const void* e_pred, const void* e_true, long n, int batch, double* loss_dev, void* grad, void* ws,
                   void* stream);
 
-/* One Adam step (bias-corrected, step >= 1) on n FP32 parameters, moments m, v. */
+/* One Adam step (the optimiser of Section 5.3; bias-corrected, step >= 1) on n FP32
+ * parameters, moments m, v. */
 int helm_adam_step(float* params, const float* grads, float* m, float* v, long n, double lr, double beta1,
                    double beta2, double eps, int step, void* stream);
 
